@@ -1,0 +1,159 @@
+/*
+ * kct.h -- C ABI of the cutting voxel projector (CVP) for NVIDIA B300 (sm_103a).
+ *
+ * Method: Kulvait & Rose, "Cutting Voxel Projector: a New Approach to Construct 3D Cone
+ * Beam CT Operator", arXiv 2110.09841. The library computes the cone-beam CT operator
+ * b = A x (Eq. fundament) and its exact adjoint x = A^T y for a float32 voxel volume and a
+ * stack of flat-panel projections, one 3x4 projection matrix per view (Sec. III-C).
+ *
+ *   b[view, v, u] = F(u, v) * S(u, v),   S = sum_vox mu_vox * W(vox, pixel)   (Eq. cvpsu)
+ *   x[vox]        = sum_view sum_pixel W(vox, pixel) * F(u, v) * y[view, v, u]
+ *
+ * W is the pair weight of the chosen variant:
+ *   KCT_CVP_EXACT    W = |V_cut| / r^2, V_cut the intersection of the voxel with the pyramid
+ *                    of all rays from the source to the pixel, r the distance from the source
+ *                    to the centre of mass of V_cut (Eq. vox, Sec. II-E, centre-of-mass r);
+ *   KCT_CVP_RELAXED  W = A_n * d / r_vox^2, A_n the area of the column cut of the voxel base,
+ *                    d the x_3 length through the centre of mass of that cut projecting into
+ *                    the pixel row, r_vox the distance to the voxel centre (Sec. III-A, Eq.
+ *                    cutvolume, Eq. vox with voxel-centre r).
+ * F is the pixel factor (Sec. III-C "second phase"):
+ *   KCT_SCALE_COS    F = f^2 / (a cos^3 theta) at the pixel centre (Eq. cvp);
+ *   KCT_SCALE_EXACT  F = 1 / abar, abar the solid angle of the pixel (Eq. cvpus).
+ *
+ * Conventions (Sec. II-A, II-B, III-A):
+ *   - the volume box is centred at the origin; voxel (i, j, k) has its centre at
+ *     ((i - (nx-1)/2) ax, (j - (ny-1)/2) ay, (k - (nz-1)/2) az) in mm;
+ *   - pixel (u, v) is the unit square around detector index coordinates (u, v);
+ *     the projection matrix maps homogeneous world points (mm) to (u, v, 1) up to scale;
+ *   - geometry must follow the paper's arrangement: the detector column index u does not
+ *     depend on x_3 (P[0][2] = P[2][2] = 0), the detector rows run along x_3 (pixels are
+ *     rectangles: the horizontal part of P row 1 is parallel to that of P row 2), and the
+ *     whole volume lies in front of the source.
+ *
+ * Memory layouts (all C-contiguous float32, device memory owned by the caller):
+ *   volume       [nz][ny][nx]          (x_1 fastest)
+ *   projections  [nviews][nv][nu]      (u fastest)
+ *
+ * Errors: every function returns a kct_status and never aborts the process. Invalid
+ * arguments are rejected before any launch. Kernel launch failures return
+ * KCT_ERR_CUDA; kct_last_error_message() gives a human-readable detail of the last
+ * failure on the calling thread.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ * kct_project and kct_backproject enqueue work only: they allocate nothing, do not
+ * synchronise and may be captured in a CUDA graph.
+ */
+#ifndef KCT_H
+#define KCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KCT_VERSION 100
+
+typedef enum kct_status {
+    KCT_OK = 0,
+    KCT_ERR_INVALID_ARG = 1,   /* null pointer, non-positive size, unknown enum value */
+    KCT_ERR_GEOMETRY = 2,      /* projection matrices violate the required arrangement */
+    KCT_ERR_CUDA = 3,          /* a CUDA runtime call or kernel launch failed */
+    KCT_ERR_OOM = 4,           /* device or host allocation failed in kct_plan_create */
+    KCT_ERR_DEVICE_CHECK = 5,  /* a kernel reported an inconsistent footprint */
+    KCT_ERR_UNSUPPORTED = 6    /* request outside what this build supports */
+} kct_status;
+
+typedef enum kct_variant {
+    KCT_CVP_EXACT = 0,         /* cut volume and centre of mass of each voxel-pixel pair */
+    KCT_CVP_RELAXED = 1        /* column area times x_3 segment at the column centre of mass */
+} kct_variant;
+
+typedef enum kct_scaling {
+    KCT_SCALE_COS = 0,         /* f^2 / (a cos^3 theta), Eq. cvp */
+    KCT_SCALE_EXACT = 1        /* 1 / solid angle of the pixel, Eq. cvpus */
+} kct_scaling;
+
+typedef struct kct_volume_desc {
+    int32_t nx, ny, nz;        /* voxels per edge (Sec. II-A: N_1, N_2, N_3) */
+    double ax, ay, az;         /* voxel size in mm (a_1, a_2, a_3) */
+} kct_volume_desc;
+
+typedef struct kct_detector_desc {
+    int32_t nu, nv;            /* pixels per row (u) and per column (v) */
+    double pu, pv;             /* pixel pitch in mm (b_1, b_2); informational */
+} kct_detector_desc;
+
+typedef struct kct_plan kct_plan;
+
+/*
+ * Create a plan for one geometry on the current CUDA device.
+ *   pmats   host pointer, float64 [nviews][3][4] row-major projection matrices mapping
+ *           (x_1, x_2, x_3, 1) in mm to homogeneous detector index coordinates; copied.
+ *   nviews  number of views, >= 1.
+ * Validates the arrangement above (KCT_ERR_GEOMETRY otherwise), converts each view to the
+ * kernel's FP32 parameters (source, principal direction, detector scales) and uploads them.
+ * The plan owns that device memory until kct_plan_destroy. Allocation failure returns
+ * KCT_ERR_OOM. On error *out is set to NULL.
+ */
+kct_status kct_plan_create(kct_plan **out, const kct_volume_desc *vol, const kct_detector_desc *det,
+                           const double *pmats, int32_t nviews, kct_variant variant,
+                           kct_scaling scaling);
+
+/* Release the plan and its device memory. Waits for nothing: the caller must make sure no
+ * work that uses the plan is still pending. NULL is accepted. */
+kct_status kct_plan_destroy(kct_plan *plan);
+
+/*
+ * Forward projection b = A x (Eq. cvpsu then the pixel factor).
+ *   d_vol   device float32 [nz][ny][nx], read only.
+ *   d_proj  device float32 [nviews][nv][nu]; overwritten (accumulate = 0) or added to
+ *           (accumulate != 0). Must not overlap d_vol.
+ * Enqueued on `stream`; returns after enqueueing. Accumulation order between voxels is
+ * not fixed (float atomics), so results can differ in the last bits between runs.
+ */
+kct_status kct_project(const kct_plan *plan, const float *d_vol, float *d_proj, int32_t accumulate,
+                       void *stream);
+
+/*
+ * Adjoint (backprojection) x = A^T y, with the same pair weights and pixel factors as
+ * kct_project, so that <A x, y> = <x, A^T y> up to float32 rounding (Sec. III-D).
+ *   d_proj  device float32 [nviews][nv][nu], read only.
+ *   d_vol   device float32 [nz][ny][nx]; overwritten (accumulate = 0) or added to.
+ * Each voxel is written by exactly one thread: the result is deterministic.
+ */
+kct_status kct_backproject(const kct_plan *plan, const float *d_proj, float *d_vol, int32_t accumulate,
+                           void *stream);
+
+/*
+ * Pixel factors F(u, v) of every view of the plan (its scaling mode) into
+ * d_out, device float32 [nviews][nv][nu]. Enqueued on `stream`.
+ */
+kct_status kct_pixel_factors(const kct_plan *plan, float *d_out, void *stream);
+
+/*
+ * Number of nonzero voxel-pixel pairs A has, counted on the device for the plan's variant
+ * (a pair counts when its weight is > 0). Synchronises `stream`.
+ */
+kct_status kct_count_pairs(const kct_plan *plan, uint64_t *count, void *stream);
+
+/* Read and clear the plan's device error word (0 = no error). Synchronises `stream`.
+ * Nonzero codes: 1 = a voxel footprint larger than the kernel's bound was skipped. */
+kct_status kct_last_device_error(const kct_plan *plan, int32_t *code, void *stream);
+
+/* Static description of a status code. */
+const char *kct_status_string(kct_status status);
+
+/* Detail of the last failure on the calling thread ("" if none). */
+const char *kct_last_error_message(void);
+
+/* KCT_VERSION of the library. */
+int32_t kct_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KCT_H */

@@ -1,0 +1,402 @@
+// kct_api.cu -- C ABI of the cutting voxel projector: plan creation, geometry validation,
+// kernel launches. See include/kct.h for the contract of every entry point.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kct.h"
+#include "cvp_device.cuh"
+#include "cvp_kernels.cuh"
+
+using kct::Grid;
+using kct::View;
+
+struct kct_plan {
+    int device;
+    kct_volume_desc vol;
+    kct_detector_desc det;
+    int32_t nviews;
+    kct_variant variant;
+    kct_scaling scaling;
+    Grid grid;
+    std::vector<View> h_views;
+    View* d_views;
+    int* d_err;
+    unsigned long long* d_count;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+kct_status fail(kct_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+
+kct_status cuda_fail(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return KCT_ERR_CUDA;
+}
+
+bool finite_all(const double* p, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+void split(double v, float& hi, float& lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
+// Convert one 3x4 projection matrix into the kernel's per-view parameters.
+// Returns an empty string on success, else the reason it violates the arrangement the
+// projector needs (Sec. III-A): u independent of x_3, rows along x_3, volume in front.
+std::string setup_view(const double* P, const kct_volume_desc& vol, View& V) {
+    if (!finite_all(P, 12)) return "non-finite matrix entry";
+    double M[3][3], p4[3];
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) M[r][c] = P[4 * r + c];
+        p4[r] = P[4 * r + 3];
+    }
+    double n0 = std::sqrt(M[0][0] * M[0][0] + M[0][1] * M[0][1] + M[0][2] * M[0][2]);
+    double n1 = std::sqrt(M[1][0] * M[1][0] + M[1][1] * M[1][1] + M[1][2] * M[1][2]);
+    double n2 = std::sqrt(M[2][0] * M[2][0] + M[2][1] * M[2][1] + M[2][2] * M[2][2]);
+    double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+                 M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                 M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+    if (!(std::fabs(det) > 1e-12 * n0 * n1 * n2)) return "singular 3x3 part";
+    if (std::fabs(M[0][2]) > 1e-9 * n0) return "detector column depends on x3 (P[0][2] != 0)";
+    if (std::fabs(M[2][2]) > 1e-9 * n2) return "principal axis not horizontal (P[2][2] != 0)";
+    // source s = -M^{-1} p4
+    double inv[3][3];
+    double id = 1.0 / det;
+    inv[0][0] = (M[1][1] * M[2][2] - M[1][2] * M[2][1]) * id;
+    inv[0][1] = (M[0][2] * M[2][1] - M[0][1] * M[2][2]) * id;
+    inv[0][2] = (M[0][1] * M[1][2] - M[0][2] * M[1][1]) * id;
+    inv[1][0] = (M[1][2] * M[2][0] - M[1][0] * M[2][2]) * id;
+    inv[1][1] = (M[0][0] * M[2][2] - M[0][2] * M[2][0]) * id;
+    inv[1][2] = (M[0][2] * M[1][0] - M[0][0] * M[1][2]) * id;
+    inv[2][0] = (M[1][0] * M[2][1] - M[1][1] * M[2][0]) * id;
+    inv[2][1] = (M[0][1] * M[2][0] - M[0][0] * M[2][1]) * id;
+    inv[2][2] = (M[0][0] * M[1][1] - M[0][1] * M[1][0]) * id;
+    double s[3];
+    for (int r = 0; r < 3; ++r) s[r] = -(inv[r][0] * p4[0] + inv[r][1] * p4[1] + inv[r][2] * p4[2]);
+    // orientation: the volume centre (origin) must be in front of the source
+    if (p4[2] == 0.0) return "volume centre on the source plane";
+    double sigma = p4[2] > 0.0 ? 1.0 : -1.0;
+    double m2h = std::sqrt(M[2][0] * M[2][0] + M[2][1] * M[2][1]);
+    double wx = sigma * M[2][0] / m2h, wy = sigma * M[2][1] / m2h;
+    double hx = -wy, hy = wx;
+    // rectangular pixels with rows along x3: horizontal part of row 1 parallel to row 2
+    double m1h_h = M[1][0] * hx + M[1][1] * hy;
+    if (std::fabs(m1h_h) > 1e-9 * n1) return "detector rows not along x3 (skewed pixel grid)";
+    if (!(std::fabs(M[1][2]) > 1e-12 * n1)) return "detector row index independent of x3";
+    double den = sigma * m2h;
+    double cu = (M[0][0] * wx + M[0][1] * wy) / den;
+    double gu = (M[0][0] * hx + M[0][1] * hy) / den;
+    double cv = (M[1][0] * wx + M[1][1] * wy) / den;
+    double gv = M[1][2] / den;
+    if (!(std::fabs(gu) > 0.0) || !(std::fabs(gv) > 0.0)) return "degenerate detector scale";
+    // whole volume in front of the source: depth t = w.(X - s) > 0 at all eight corners
+    double lx = 0.5 * vol.nx * vol.ax, ly = 0.5 * vol.ny * vol.ay;
+    double tmin = 1e300;
+    for (int c = 0; c < 4; ++c) {
+        double X = (c & 1) ? lx : -lx, Y = (c & 2) ? ly : -ly;
+        tmin = std::fmin(tmin, wx * (X - s[0]) + wy * (Y - s[1]));
+    }
+    double diag = std::sqrt(vol.ax * vol.ax + vol.ay * vol.ay);
+    if (!(tmin > diag)) return "source inside or too close to the volume";
+    split(wx, V.wx, V.wx_lo);
+    split(wy, V.wy, V.wy_lo);
+    split(-(wx * s[0] + wy * s[1]), V.aw, V.aw_lo);
+    V.ah = (float)(-(hx * s[0] + hy * s[1]));
+    V.sz = (float)s[2];
+    V.cu = (float)cu;
+    V.gu = (float)gu;
+    V.cv = (float)cv;
+    V.gv = (float)gv;
+    V.igu = (float)(1.0 / gu);
+    V.igv = (float)(1.0 / gv);
+    V.inv_agv = (float)(1.0 / std::fabs(gv));
+    V.sgv = gv > 0.0 ? 1.0f : -1.0f;
+    V.fcos = (float)std::fabs(gu * gv);
+    // base square of a voxel, counter-clockwise in (x1, x2); (t', xi') = (w.q, h.q)
+    const double qx[4] = {-0.5 * vol.ax, 0.5 * vol.ax, 0.5 * vol.ax, -0.5 * vol.ax};
+    const double qy[4] = {-0.5 * vol.ay, -0.5 * vol.ay, 0.5 * vol.ay, 0.5 * vol.ay};
+    double tt[4], xx[4];
+    double tmn = 1e300, tmx = -1e300;
+    for (int e = 0; e < 4; ++e) {
+        tt[e] = wx * qx[e] + wy * qy[e];
+        xx[e] = hx * qx[e] + hy * qy[e];
+        V.sq_t[e] = (float)tt[e];
+        V.sq_x[e] = (float)xx[e];
+        tmn = std::fmin(tmn, tt[e]);
+        tmx = std::fmax(tmx, tt[e]);
+    }
+    V.tmin_sq = (float)tmn;
+    V.tmax_sq = (float)tmx;
+    double stt = 0.0, stx = 0.0;
+    for (int e = 0; e < 4; ++e) {
+        int f = (e + 1) & 3;
+        double c = tt[e] * xx[f] - tt[f] * xx[e];
+        stt += c * (tt[e] * tt[e] + tt[e] * tt[f] + tt[f] * tt[f]);
+        stx += c * (2 * tt[e] * xx[e] + tt[e] * xx[f] + tt[f] * xx[e] + 2 * tt[f] * xx[f]);
+    }
+    V.sq_tt = (float)stt;
+    V.sq_tx = (float)stx;
+    V.pad[0] = V.pad[1] = 0.f;
+    return std::string();
+}
+
+template <int VARIANT, int SCALING>
+void launch_fwd(const kct_plan* p, const float* vol, float* proj, cudaStream_t st) {
+    const Grid& G = p->grid;
+    const int threads = 128;
+    const int kchunk = 32;
+    dim3 grid((G.nx * G.ny + threads - 1) / threads, G.nviews, (G.nz + kchunk - 1) / kchunk);
+    kct::fwd_atomic_kernel<VARIANT, SCALING><<<grid, threads, 0, st>>>(p->d_views, G, vol, proj, kchunk, p->d_err);
+}
+
+template <int VARIANT, int SCALING>
+void launch_bwd(const kct_plan* p, const float* proj, float* vol, int accumulate, cudaStream_t st) {
+    const Grid& G = p->grid;
+    const int threads = 128;
+    long nvox = (long)G.nx * G.ny * G.nz;
+    dim3 grid((unsigned)((nvox + threads - 1) / threads));
+    kct::bwd_gather_kernel<VARIANT, SCALING><<<grid, threads, 0, st>>>(p->d_views, G, proj, vol, accumulate, p->d_err);
+}
+
+template <int VARIANT>
+void launch_count(const kct_plan* p, cudaStream_t st) {
+    const Grid& G = p->grid;
+    const int threads = 128;
+    const int kchunk = 32;
+    dim3 grid((G.nx * G.ny + threads - 1) / threads, G.nviews, (G.nz + kchunk - 1) / kchunk);
+    kct::count_kernel<VARIANT><<<grid, threads, 0, st>>>(p->d_views, G, kchunk, p->d_count, p->d_err);
+}
+
+kct_status check_plan(const kct_plan* p) {
+    if (!p) return fail(KCT_ERR_INVALID_ARG, "null plan");
+    return KCT_OK;
+}
+
+kct_status set_device(const kct_plan* p) {
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (cur != p->device) {
+        e = cudaSetDevice(p->device);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    }
+    return KCT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t kct_version(void) { return KCT_VERSION; }
+
+const char* kct_status_string(kct_status s) {
+    switch (s) {
+        case KCT_OK: return "ok";
+        case KCT_ERR_INVALID_ARG: return "invalid argument";
+        case KCT_ERR_GEOMETRY: return "geometry outside the projector's arrangement";
+        case KCT_ERR_CUDA: return "CUDA error";
+        case KCT_ERR_OOM: return "out of memory";
+        case KCT_ERR_DEVICE_CHECK: return "device-side check failed";
+        case KCT_ERR_UNSUPPORTED: return "unsupported request";
+    }
+    return "unknown status";
+}
+
+const char* kct_last_error_message(void) { return g_last_error.c_str(); }
+
+kct_status kct_plan_create(kct_plan** out, const kct_volume_desc* vol, const kct_detector_desc* det,
+                           const double* pmats, int32_t nviews, kct_variant variant, kct_scaling scaling) {
+    g_last_error.clear();
+    if (!out) return fail(KCT_ERR_INVALID_ARG, "null output pointer");
+    *out = nullptr;
+    if (!vol || !det || !pmats) return fail(KCT_ERR_INVALID_ARG, "null descriptor or matrix pointer");
+    if (vol->nx <= 0 || vol->ny <= 0 || vol->nz <= 0) return fail(KCT_ERR_INVALID_ARG, "volume sizes must be positive");
+    if (!(vol->ax > 0.0) || !(vol->ay > 0.0) || !(vol->az > 0.0) || !std::isfinite(vol->ax) ||
+        !std::isfinite(vol->ay) || !std::isfinite(vol->az))
+        return fail(KCT_ERR_INVALID_ARG, "voxel sizes must be positive and finite");
+    if (det->nu <= 0 || det->nv <= 0) return fail(KCT_ERR_INVALID_ARG, "detector sizes must be positive");
+    if (!(det->pu > 0.0) || !(det->pv > 0.0)) return fail(KCT_ERR_INVALID_ARG, "pixel pitch must be positive");
+    if (nviews <= 0 || nviews > 65535) return fail(KCT_ERR_INVALID_ARG, "nviews must be in [1, 65535]");
+    if (variant != KCT_CVP_EXACT && variant != KCT_CVP_RELAXED) return fail(KCT_ERR_INVALID_ARG, "unknown variant");
+    if (scaling != KCT_SCALE_COS && scaling != KCT_SCALE_EXACT) return fail(KCT_ERR_INVALID_ARG, "unknown scaling");
+    long long nvox = (long long)vol->nx * vol->ny * vol->nz;
+    long long npix = (long long)det->nu * det->nv * nviews;
+    if (nvox > (1LL << 31) - 1 || npix > (1LL << 40)) return fail(KCT_ERR_UNSUPPORTED, "problem too large for 32-bit voxel indexing");
+    if ((long long)vol->nx * vol->ny > (1LL << 31) - 1) return fail(KCT_ERR_UNSUPPORTED, "volume slice too large");
+
+    kct_plan* p = new (std::nothrow) kct_plan();
+    if (!p) return fail(KCT_ERR_OOM, "host allocation of the plan");
+    p->vol = *vol;
+    p->det = *det;
+    p->nviews = nviews;
+    p->variant = variant;
+    p->scaling = scaling;
+    p->d_views = nullptr;
+    p->d_err = nullptr;
+    p->d_count = nullptr;
+    p->h_views.resize(nviews);
+    for (int q = 0; q < nviews; ++q) {
+        std::string why = setup_view(pmats + 12 * q, *vol, p->h_views[q]);
+        if (!why.empty()) {
+            delete p;
+            char buf[64];
+            std::snprintf(buf, sizeof buf, "view %d: ", q);
+            return fail(KCT_ERR_GEOMETRY, buf + why);
+        }
+    }
+    Grid& G = p->grid;
+    G.nx = vol->nx; G.ny = vol->ny; G.nz = vol->nz;
+    G.nu = det->nu; G.nv = det->nv; G.nviews = nviews;
+    G.ax = (float)vol->ax; G.ay = (float)vol->ay; G.az = (float)vol->az;
+    G.x0 = (float)(0.5 * (1 - vol->nx) * vol->ax);
+    G.y0 = (float)(0.5 * (1 - vol->ny) * vol->ay);
+    G.z0 = (float)(0.5 * (1 - vol->nz) * vol->az);
+
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) { delete p; return cuda_fail(e, "cudaGetDevice"); }
+    e = cudaMalloc(&p->d_views, sizeof(View) * nviews);
+    if (e != cudaSuccess) { delete p; return fail(KCT_ERR_OOM, std::string("cudaMalloc views: ") + cudaGetErrorString(e)); }
+    e = cudaMalloc(&p->d_err, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_count, sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        cudaFree(p->d_views);
+        cudaFree(p->d_err);
+        delete p;
+        return fail(KCT_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    e = cudaMemcpy(p->d_views, p->h_views.data(), sizeof(View) * nviews, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int) * 4);
+    if (e != cudaSuccess) {
+        cudaFree(p->d_views); cudaFree(p->d_err); cudaFree(p->d_count);
+        delete p;
+        return cuda_fail(e, "uploading view parameters");
+    }
+    *out = p;
+    return KCT_OK;
+}
+
+kct_status kct_plan_destroy(kct_plan* p) {
+    if (!p) return KCT_OK;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != p->device) cudaSetDevice(p->device);
+    cudaFree(p->d_views);
+    cudaFree(p->d_err);
+    cudaFree(p->d_count);
+    if (cur >= 0 && cur != p->device) cudaSetDevice(cur);
+    delete p;
+    return KCT_OK;
+}
+
+kct_status kct_project(const kct_plan* p, const float* d_vol, float* d_proj, int32_t accumulate, void* stream) {
+    kct_status s = check_plan(p);
+    if (s != KCT_OK) return s;
+    if (!d_vol || !d_proj) return fail(KCT_ERR_INVALID_ARG, "null data pointer");
+    if ((s = set_device(p)) != KCT_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const Grid& G = p->grid;
+    size_t pbytes = sizeof(float) * (size_t)G.nu * G.nv * G.nviews;
+    cudaError_t e;
+    if (!accumulate) {
+        e = cudaMemsetAsync(d_proj, 0, pbytes, st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    }
+    int key = (p->variant == KCT_CVP_RELAXED ? 2 : 0) + (p->scaling == KCT_SCALE_EXACT ? 1 : 0);
+    switch (key) {
+        case 0: launch_fwd<0, 0>(p, d_vol, d_proj, st); break;
+        case 1: launch_fwd<0, 1>(p, d_vol, d_proj, st); break;
+        case 2: launch_fwd<1, 0>(p, d_vol, d_proj, st); break;
+        default: launch_fwd<1, 1>(p, d_vol, d_proj, st); break;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "forward projection launch");
+    return KCT_OK;
+}
+
+kct_status kct_backproject(const kct_plan* p, const float* d_proj, float* d_vol, int32_t accumulate, void* stream) {
+    kct_status s = check_plan(p);
+    if (s != KCT_OK) return s;
+    if (!d_vol || !d_proj) return fail(KCT_ERR_INVALID_ARG, "null data pointer");
+    if ((s = set_device(p)) != KCT_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    int key = (p->variant == KCT_CVP_RELAXED ? 2 : 0) + (p->scaling == KCT_SCALE_EXACT ? 1 : 0);
+    int acc = accumulate ? 1 : 0;
+    switch (key) {
+        case 0: launch_bwd<0, 0>(p, d_proj, d_vol, acc, st); break;
+        case 1: launch_bwd<0, 1>(p, d_proj, d_vol, acc, st); break;
+        case 2: launch_bwd<1, 0>(p, d_proj, d_vol, acc, st); break;
+        default: launch_bwd<1, 1>(p, d_proj, d_vol, acc, st); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "backprojection launch");
+    return KCT_OK;
+}
+
+kct_status kct_pixel_factors(const kct_plan* p, float* d_out, void* stream) {
+    kct_status s = check_plan(p);
+    if (s != KCT_OK) return s;
+    if (!d_out) return fail(KCT_ERR_INVALID_ARG, "null output pointer");
+    if ((s = set_device(p)) != KCT_OK) return s;
+    const Grid& G = p->grid;
+    long n = (long)G.nu * G.nv;
+    dim3 grid((unsigned)((n + 255) / 256), G.nviews);
+    if (p->scaling == KCT_SCALE_EXACT)
+        kct::factor_kernel<1><<<grid, 256, 0, (cudaStream_t)stream>>>(p->d_views, G, d_out);
+    else
+        kct::factor_kernel<0><<<grid, 256, 0, (cudaStream_t)stream>>>(p->d_views, G, d_out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "pixel factor launch");
+    return KCT_OK;
+}
+
+kct_status kct_count_pairs(const kct_plan* p, uint64_t* count, void* stream) {
+    kct_status s = check_plan(p);
+    if (s != KCT_OK) return s;
+    if (!count) return fail(KCT_ERR_INVALID_ARG, "null output pointer");
+    if ((s = set_device(p)) != KCT_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(p->d_count, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    if (p->variant == KCT_CVP_RELAXED) launch_count<1>(p, st);
+    else launch_count<0>(p, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "pair count launch");
+    unsigned long long h = 0;
+    e = cudaMemcpyAsync(&h, p->d_count, sizeof h, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the pair count");
+    *count = (uint64_t)h;
+    return KCT_OK;
+}
+
+kct_status kct_last_device_error(const kct_plan* p, int32_t* code, void* stream) {
+    kct_status s = check_plan(p);
+    if (s != KCT_OK) return s;
+    if (!code) return fail(KCT_ERR_INVALID_ARG, "null output pointer");
+    if ((s = set_device(p)) != KCT_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
+    *code = h;
+    return KCT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,188 @@
+"""GPU parity: the CUDA projector (through the C ABI) against the FP64 CPU oracle.
+
+Tolerance (float32 arithmetic with float atomics): per view, over pixels whose oracle
+value is at least 1e-3 of that view's maximum, max |gpu - oracle| / |oracle| <= 1e-4, and
+over all pixels max |gpu - oracle| <= 1e-4 * view maximum; the same rule over voxels for
+the adjoint. Adjoint identity <A x, y> = <x, A^T y> with float64 dot products to 1e-5.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2110_09841_b300 import inputs
+from paper_2110_09841_b300.kct import Projector
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = [("exact", 0), ("relaxed", 1)]
+SCALINGS = [("cos", 0), ("exact", 1)]
+TOL = 1e-4
+
+
+def assert_close_per_view(g, o, tol=TOL, what="projection"):
+    g = np.asarray(g, dtype=np.float64)
+    o = np.asarray(o, dtype=np.float64)
+    assert g.shape == o.shape
+    worst_rel = worst_abs = 0.0
+    for view in range(o.shape[0]):
+        mx = np.abs(o[view]).max()
+        if mx == 0.0:
+            assert np.abs(g[view]).max() <= 1e-30, f"{what} view {view} should be empty"
+            continue
+        d = np.abs(g[view] - o[view])
+        big = np.abs(o[view]) >= 1e-3 * mx
+        worst_rel = max(worst_rel, float((d[big] / np.abs(o[view][big])).max()))
+        worst_abs = max(worst_abs, float(d.max() / mx))
+    assert worst_rel <= tol, f"{what}: max relative error {worst_rel:.3e}"
+    assert worst_abs <= tol, f"{what}: max error / view max {worst_abs:.3e}"
+    return worst_rel, worst_abs
+
+
+def assert_close_volume(g, o, tol=TOL):
+    return assert_close_per_view(np.asarray(g)[None], np.asarray(o)[None], tol, "backprojection")
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+@pytest.fixture(scope="module")
+def cvp32():
+    g = inputs.workload_geometry("cvp32")
+    x = inputs.workload_phantom("cvp32").numpy()
+    y = inputs.uniform_projections(g.proj_shape, 2024).numpy()
+    return g, x, y
+
+
+@pytest.mark.parametrize("vname,variant", VARIANTS)
+@pytest.mark.parametrize("sname,scaling", SCALINGS)
+def test_project_cvp32(cvp32, vname, variant, sname, scaling):
+    g, x, y = cvp32
+    ref = oracle.project(g, x.astype(np.float64), variant, scaling)
+    A = Projector(g, vname, sname)
+    b = A.project(dev(x))
+    torch.cuda.synchronize()
+    assert A.device_error() == 0
+    assert_close_per_view(b.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("vname,variant", VARIANTS)
+@pytest.mark.parametrize("sname,scaling", SCALINGS)
+def test_backproject_cvp32(cvp32, vname, variant, sname, scaling):
+    g, x, y = cvp32
+    ref = oracle.backproject(g, y.astype(np.float64), variant, scaling)
+    A = Projector(g, vname, sname)
+    xb = A.backproject(dev(y))
+    torch.cuda.synchronize()
+    assert A.device_error() == 0
+    assert_close_volume(xb.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("vname", ["exact", "relaxed"])
+@pytest.mark.parametrize("name", ["cvp32", "ragged"])
+def test_adjoint_gap(vname, name):
+    if name == "cvp32":
+        g = inputs.workload_geometry("cvp32")
+    else:
+        g = inputs.make_geometry((13, 7, 11), (0.9, 1.3, 0.7), (37, 29), (0.7, 0.9), 5, 300.0, 500.0, 170.0)
+    x = inputs.uniform_volume(g.vol_shape, 11, device="cuda")
+    y = inputs.uniform_projections(g.proj_shape, 12, device="cuda")
+    A = Projector(g, vname, "cos")
+    Ax = A.project(x).double()
+    Aty = A.backproject(y).double()
+    lhs = float((Ax * y.double()).sum())
+    rhs = float((x.double() * Aty).sum())
+    gap = abs(lhs - rhs) / max(abs(lhs), abs(rhs))
+    assert gap <= 1e-5, gap
+
+
+@pytest.mark.parametrize("vname,variant", VARIANTS)
+def test_ragged_and_truncated(vname, variant):
+    """Odd sizes, anisotropic voxels, a detector that truncates the volume, half-integer
+    principal point, views at 0 and 90 degrees (boundaries through voxel faces)."""
+    g = inputs.make_geometry((13, 7, 11), (0.9, 1.3, 0.7), (17, 9), (0.7, 0.9), 4, 300.0, 500.0, 360.0)
+    x = np.random.default_rng(3).random(g.vol_shape)
+    y = np.random.default_rng(4).random(g.proj_shape)
+    A = Projector(g, vname, "cos")
+    b = A.project(dev(x)).cpu().numpy()
+    assert_close_per_view(b, oracle.project(g, x, variant, 0))
+    xb = A.backproject(dev(y)).cpu().numpy()
+    assert_close_volume(xb, oracle.backproject(g, y, variant, 0))
+
+
+def test_single_voxel_and_accumulate():
+    g = inputs.make_geometry((1, 1, 1), (2.0, 2.0, 2.0), (12, 12), (0.5, 0.5), 3, 400.0, 600.0, 360.0)
+    x = np.ones(g.vol_shape)
+    A = Projector(g, "exact", "cos")
+    b = A.project(dev(x)).cpu().numpy()
+    assert_close_per_view(b, oracle.project(g, x, 0, 0))
+    out = dev(np.full(g.proj_shape, 0.25))
+    A.project(dev(x), out=out, accumulate=True)
+    assert_close_per_view(out.cpu().numpy() - 0.25, oracle.project(g, x, 0, 0), tol=1e-4)
+    xb = dev(np.full(g.vol_shape, 2.0))
+    y = np.ones(g.proj_shape)
+    A.backproject(dev(y), out=xb, accumulate=True)
+    ref = oracle.backproject(g, y, 0, 0) + 2.0
+    assert abs(float(xb.cpu()[0, 0, 0]) - ref[0, 0, 0]) <= 1e-5 * ref[0, 0, 0]
+
+
+def test_volume_off_detector_gives_zeros():
+    # a detector far off to the side: no voxel projects onto it
+    P = inputs.circular_pmats(2, 300.0, 500.0, 16, 16, 0.5, 0.5, cu=-400.0)
+    g = inputs.Geometry(8, 8, 8, 1.0, 1.0, 1.0, 16, 16, 0.5, 0.5, P)
+    A = Projector(g, "exact", "cos")
+    b = A.project(dev(np.ones(g.vol_shape)))
+    assert float(b.abs().max()) == 0.0
+    xb = A.backproject(dev(np.ones(g.proj_shape)))
+    assert float(xb.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("sname,scaling", SCALINGS)
+def test_pixel_factors(sname, scaling):
+    g = inputs.workload_geometry("cvp256").subset_views([0, 77, 200])
+    A = Projector(g, "exact", sname)
+    F = A.pixel_factors().cpu().numpy()
+    rng = np.random.default_rng(5)
+    for view in range(3):
+        for u, v in list(zip(rng.integers(0, g.nu, 20), rng.integers(0, g.nv, 20))) + [(0, 0), (g.nu - 1, g.nv - 1)]:
+            ref = oracle.pixel_factor(g.pmats[view], u, v, scaling)
+            assert F[view, v, u] == pytest.approx(ref, rel=2e-6)
+
+
+def sampled_pixels(g, rng, views, per_view):
+    pix = []
+    for view in views:
+        for _ in range(per_view):
+            pix.append((view, int(rng.integers(0, g.nv)), int(rng.integers(0, g.nu))))
+    return np.array(pix, dtype=np.int32)
+
+
+@pytest.mark.parametrize("name", ["cvp256", "cvp512"])
+@pytest.mark.parametrize("vname,variant", VARIANTS)
+def test_sampled_parity_full_size(name, vname, variant):
+    """Full-size workload, projected in full on the GPU; the oracle computes sampled
+    pixels one by one."""
+    g = inputs.workload_geometry(name)
+    x = inputs.workload_phantom(name, device="cuda")
+    A = Projector(g, vname, "cos")
+    b = A.project(x)
+    torch.cuda.synchronize()
+    assert A.device_error() == 0
+    rng = np.random.default_rng(77)
+    views = [0, g.nviews // 3, g.nviews - 1]
+    # pixels where the phantom projects (nonzero), plus random ones
+    bc = b.cpu().numpy()
+    pix = []
+    for view in views:
+        nz = np.argwhere(bc[view] > 0.05 * bc[view].max())
+        sel = nz[rng.choice(len(nz), 12, replace=False)]
+        pix += [(view, int(r), int(c)) for r, c in sel]
+    pix = np.array(pix + [tuple(p) for p in sampled_pixels(g, rng, views, 4)], dtype=np.int32)
+    ref = oracle.project_pixels(g, x.cpu().numpy(), pix, variant, 0)
+    got = bc[pix[:, 0], pix[:, 1], pix[:, 2]]
+    vmax = np.array([bc[v].max() for v in pix[:, 0]])
+    err = np.abs(got - ref)
+    assert np.all(err <= TOL * vmax), float((err / vmax).max())
+    big = ref >= 1e-3 * vmax
+    assert np.all(err[big] <= TOL * ref[big]), float((err[big] / ref[big]).max())
