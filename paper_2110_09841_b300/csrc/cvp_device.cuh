@@ -322,187 +322,4 @@ __device__ __forceinline__ Mom cpm(const View& V, const Column& C, int kind, flo
     return normalise(g, C.tc, C.xc);
 }
 
-template <class Emit>
-__device__ __forceinline__ void exact_column(const View& V, const Grid& G, int i, int j, int k0, int k1,
-                                             Emit& emit, int* err) {
-    Column C;
-    if (!column_setup(V, G, i, j, C)) return;
-    if (C.n_last - C.n_first + 2 > KCT_MAX_SPAN) { atomicOr(err, 1); return; }
-    const float az = G.az;
-    // the full square (centred): m1 = ax ay, first moments 0
-    Mom sq;
-    sq.m1 = G.ax * G.ay;
-    sq.mt = 0.f;
-    sq.mtt = V.sq_tt * (1.f / 12.f);
-    sq.ml = 0.f;
-    sq.mlt = fmaf(C.tc, sq.mtt, C.xc * (V.sq_tx * (1.f / 24.f)));
-
-    for (int cstart = C.n_first; cstart <= C.n_last; cstart += KCT_CB - 1) {
-        const int ncol = min(KCT_CB - 1, C.n_last - cstart + 1);
-        const int nb = ncol + 1;
-        int kind[KCT_CB];
-        float l1t[KCT_CB], l1c[KCT_CB];
-        Mom full[KCT_CB];
-#pragma unroll
-        for (int c = 0; c < KCT_CB; ++c) {
-            kind[c] = KIND_EMPTY;
-            l1t[c] = 0.f;
-            l1c[c] = 0.f;
-            full[c] = Mom{0.f, 0.f, 0.f, 0.f, 0.f};
-            if (c < nb) {
-                float U = (float)(cstart + c) - 0.5f;
-                // u < U  <=>  gu xi' + (cu - U) t' + tc (u_c - U) < 0, divided by tc
-                l1t[c] = (V.cu - U) * C.itc;
-                l1c[c] = -fmaf(V.gu, C.alc, V.cu - U);   // U - u_c
-                if (U <= C.umin) kind[c] = KIND_EMPTY;
-                else if (U >= C.umax) { kind[c] = KIND_FULL; full[c] = sq; }
-                else {
-                    kind[c] = KIND_GEN;
-                    full[c] = normalise(region<true, false, true>(V, l1t[c], C.gxi, l1c[c], 0.f), C.tc, C.xc);
-                }
-            }
-        }
-        for (int k = k0; k < k1; ++k) {
-            Slice S;
-            if (!slice_setup(V, G, C, k, S)) continue;
-            if (S.m_last - S.m_first + 2 > KCT_MAX_SPAN) { atomicOr(err, 1); continue; }
-            emit.begin(k);
-            const float D2 = fmaf(C.tc, C.tc, fmaf(C.xc, C.xc, S.zc * S.zc));
-            const float zs = S.zc * V.sgv;
-            float pV[KCT_CB], pQ[KCT_CB];
-#pragma unroll
-            for (int c = 0; c < KCT_CB; ++c) { pV[c] = 0.f; pQ[c] = 0.f; }
-            const int R = S.m_last - S.m_first + 1;
-            for (int b = 0; b <= R; ++b) {
-                const float Vb = (float)(S.m_first + b) - 0.5f;
-                float gV[KCT_CB], gQ[KCT_CB];
-                if (Vb <= S.vmin) {
-#pragma unroll
-                    for (int c = 0; c < KCT_CB; ++c) { gV[c] = 0.f; gQ[c] = 0.f; }
-                } else if (Vb >= S.vmax) {
-#pragma unroll
-                    for (int c = 0; c < KCT_CB; ++c) { gV[c] = az * full[c].m1; gQ[c] = az * full[c].ml; }
-                } else {
-                    float p0, p1;
-                    row_plane(V, G, C, S, Vb, p0, p1);
-                    float p1s = (fabsf(p1) < 1e-30f) ? copysignf(1e-30f, p1) : p1;
-                    float tau0 = -p0 / p1s, tau1 = (az - p0) / p1s;
-#pragma unroll
-                    for (int c = 0; c < KCT_CB; ++c) {
-                        gV[c] = 0.f;
-                        gQ[c] = 0.f;
-                        if (c < nb && kind[c] != KIND_EMPTY) {
-                            Mom c0 = cpm(V, C, kind[c], l1t[c], l1c[c], full[c], tau0);
-                            Mom c1 = cpm(V, C, kind[c], l1t[c], l1c[c], full[c], tau1);
-                            Mom lin, fu;
-                            if (p1s > 0.f) { lin = mom_sub(c1, c0); fu = mom_sub(full[c], c1); }
-                            else { lin = mom_sub(c0, c1); fu = c1; }
-                            float Vg = fmaf(p0, lin.m1, fmaf(p1, lin.mt, az * fu.m1));
-                            float Sl = fmaf(p0, lin.ml, fmaf(p1, lin.mlt, az * fu.ml));
-                            float Sh2 = fmaf(p0 * p0, lin.m1, fmaf(2.f * p0 * p1, lin.mt,
-                                             fmaf(p1 * p1, lin.mtt, az * az * fu.m1)));
-                            gV[c] = Vg;
-                            gQ[c] = fmaf(zs, fmaf(0.5f, Sh2, -0.5f * az * Vg), Sl);
-                        }
-                    }
-                }
-                if (b > 0) {
-                    const int m = S.m_first + b - 1;
-                    const float vtiny = 1e-9f * G.ax * G.ay * az;
-#pragma unroll
-                    for (int c = 0; c + 1 < KCT_CB; ++c) {
-                        if (c + 1 < nb) {
-                            float Vp = (gV[c + 1] - gV[c]) - (pV[c + 1] - pV[c]);
-                            float Qp = (gQ[c + 1] - gQ[c]) - (pQ[c + 1] - pQ[c]);
-                            if (Vp > vtiny) {
-                                float den = fmaf(Vp, D2, 2.f * Qp);
-                                float W = Vp * Vp / den;
-                                emit.pair(k, cstart + c, m, W);
-                            }
-                        }
-                    }
-                }
-#pragma unroll
-                for (int c = 0; c < KCT_CB; ++c) { pV[c] = gV[c]; pQ[c] = gQ[c]; }
-            }
-            emit.end(k);
-        }
-    }
-}
-
-// ----------------------------------------------------------------------------------------
-// Relaxed variant
-// ----------------------------------------------------------------------------------------
-
-template <class Emit>
-__device__ __forceinline__ void relaxed_column(const View& V, const Grid& G, int i, int j, int k0, int k1,
-                                               Emit& emit, int* err) {
-    Column C;
-    if (!column_setup(V, G, i, j, C)) return;
-    if (C.n_last - C.n_first + 2 > KCT_MAX_SPAN) { atomicOr(err, 1); return; }
-    const float az = G.az;
-    const float sq_area = G.ax * G.ay;
-    for (int cstart = C.n_first; cstart <= C.n_last; cstart += KCT_CB - 1) {
-        const int ncol = min(KCT_CB - 1, C.n_last - cstart + 1);
-        const int nb = ncol + 1;
-        float A[KCT_CB], T[KCT_CB];    // area and t'-moment of P_c
-#pragma unroll
-        for (int c = 0; c < KCT_CB; ++c) {
-            A[c] = 0.f;
-            T[c] = 0.f;
-            if (c < nb) {
-                float U = (float)(cstart + c) - 0.5f;
-                if (U >= C.umax) { A[c] = sq_area; T[c] = 0.f; }
-                else if (U > C.umin) {
-                    float l1t = (V.cu - U) * C.itc;
-                    float l1c = -fmaf(V.gu, C.alc, V.cu - U);
-                    Mom5 g = region<true, false, false>(V, l1t, C.gxi, l1c, 0.f);
-                    A[c] = 0.5f * g.a;
-                    T[c] = g.t * (1.f / 6.f);
-                }
-            }
-        }
-        float An[KCT_CB - 1], Tn[KCT_CB - 1];   // area and centre-of-mass depth of H_n
-#pragma unroll
-        for (int c = 0; c + 1 < KCT_CB; ++c) {
-            An[c] = A[c + 1] - A[c];
-            Tn[c] = (An[c] > 0.f) ? (T[c + 1] - T[c]) / An[c] : 0.f;
-        }
-        for (int k = k0; k < k1; ++k) {
-            Slice S;
-            if (!slice_setup(V, G, C, k, S)) continue;
-            if (S.m_last - S.m_first + 2 > KCT_MAX_SPAN) { atomicOr(err, 1); continue; }
-            emit.begin(k);
-            const float iD2 = 1.0f / fmaf(C.tc, C.tc, fmaf(C.xc, C.xc, S.zc * S.zc));
-            const float atiny = 1e-9f * sq_area;
-            float ph[KCT_CB - 1];
-#pragma unroll
-            for (int c = 0; c + 1 < KCT_CB; ++c) ph[c] = 0.f;
-            const int R = S.m_last - S.m_first + 1;
-            for (int b = 0; b <= R; ++b) {
-                const float Vb = (float)(S.m_first + b) - 0.5f;
-                float p0, p1;
-                row_plane(V, G, C, S, Vb, p0, p1);
-#pragma unroll
-                for (int c = 0; c + 1 < KCT_CB; ++c) {
-                    float h = fminf(fmaxf(fmaf(p1, Tn[c], p0), 0.f), az);
-                    if (b > 0 && c + 1 < nb && An[c] > atiny) {
-                        float d = h - ph[c];
-                        if (d > 0.f) emit.pair(k, cstart + c, S.m_first + b - 1, An[c] * d * iD2);
-                    }
-                    ph[c] = h;
-                }
-            }
-            emit.end(k);
-        }
-    }
-}
-
-template <int VARIANT, class Emit>
-__device__ __forceinline__ void column_pairs(const View& V, const Grid& G, int i, int j, int k0, int k1,
-                                             Emit& emit, int* err) {
-    if (VARIANT == 1) relaxed_column(V, G, i, j, k0, k1, emit, err);
-    else exact_column(V, G, i, j, k0, k1, emit, err);
-}
-
 }  // namespace kct

@@ -28,6 +28,7 @@ struct kct_plan {
     View* d_views;
     int* d_err;
     unsigned long long* d_count;
+    float* d_work;      // projection-sized workspace: unscaled sums / pixel-scaled input
 };
 
 namespace {
@@ -113,6 +114,11 @@ std::string setup_view(const double* P, const kct_volume_desc& vol, View& V) {
     }
     double diag = std::sqrt(vol.ax * vol.ax + vol.ay * vol.ay);
     if (!(tmin > diag)) return "source inside or too close to the volume";
+    // rows spanned by one voxel: |gv| * (range of zeta / t over the voxel) + 2
+    double zabs = std::fmax(std::fabs(0.5 * vol.nz * vol.az - s[2]), std::fabs(-0.5 * vol.nz * vol.az - s[2]));
+    double tnear = tmin - 0.5 * diag;
+    double rows = std::fabs(gv) * (vol.az / tnear + zabs * diag / (tnear * tnear)) + 2.0;
+    if (rows > kct::KCT_ROWS - 2) return "unsupported: a voxel would span more than 30 detector rows";
     split(wx, V.wx, V.wx_lo);
     split(wy, V.wy, V.wy_lo);
     split(-(wx * s[0] + wy * s[1]), V.aw, V.aw_lo);
@@ -155,31 +161,39 @@ std::string setup_view(const double* P, const kct_volume_desc& vol, View& V) {
     return std::string();
 }
 
-template <int VARIANT, int SCALING>
-void launch_fwd(const kct_plan* p, const float* vol, float* proj, cudaStream_t st) {
-    const Grid& G = p->grid;
-    const int threads = 128;
-    const int kchunk = 32;
-    dim3 grid((G.nx * G.ny + threads - 1) / threads, G.nviews, (G.nz + kchunk - 1) / kchunk);
-    kct::fwd_atomic_kernel<VARIANT, SCALING><<<grid, threads, 0, st>>>(p->d_views, G, vol, proj, kchunk, p->d_err);
+dim3 column_grid(const Grid& G, int third) {
+    const unsigned patches = (unsigned)(((G.nx + 1) / 2) * ((G.ny + 1) / 2));
+    return dim3(patches, (unsigned)third, (unsigned)((G.nz + kct::SEG - 1) / kct::SEG));
 }
 
-template <int VARIANT, int SCALING>
-void launch_bwd(const kct_plan* p, const float* proj, float* vol, int accumulate, cudaStream_t st) {
+template <int VARIANT>
+void launch_fwd(const kct_plan* p, const float* vol, float* S, cudaStream_t st) {
+    kct::fwd_kernel<VARIANT><<<column_grid(p->grid, p->grid.nviews), 32 * kct::WARPS, 0, st>>>(
+        p->d_views, p->grid, vol, S, p->d_err);
+}
+
+template <int VARIANT>
+void launch_bwd(const kct_plan* p, const float* yF, float* vol, int accumulate, cudaStream_t st) {
+    dim3 g = column_grid(p->grid, 1);
+    g.y = g.z;
+    g.z = 1;
+    kct::bwd_kernel<VARIANT><<<g, 32 * kct::WARPS, 0, st>>>(p->d_views, p->grid, yF, vol, accumulate, p->d_err);
+}
+
+void launch_scale(const kct_plan* p, const float* in, float* out, int accumulate, cudaStream_t st) {
     const Grid& G = p->grid;
-    const int threads = 128;
-    long nvox = (long)G.nx * G.ny * G.nz;
-    dim3 grid((unsigned)((nvox + threads - 1) / threads));
-    kct::bwd_gather_kernel<VARIANT, SCALING><<<grid, threads, 0, st>>>(p->d_views, G, proj, vol, accumulate, p->d_err);
+    long n = (long)G.nu * G.nv;
+    dim3 grid((unsigned)((n + 255) / 256), G.nviews);
+    if (p->scaling == KCT_SCALE_EXACT)
+        kct::scale_kernel<1><<<grid, 256, 0, st>>>(p->d_views, G, in, out, accumulate);
+    else
+        kct::scale_kernel<0><<<grid, 256, 0, st>>>(p->d_views, G, in, out, accumulate);
 }
 
 template <int VARIANT>
 void launch_count(const kct_plan* p, cudaStream_t st) {
-    const Grid& G = p->grid;
-    const int threads = 128;
-    const int kchunk = 32;
-    dim3 grid((G.nx * G.ny + threads - 1) / threads, G.nviews, (G.nz + kchunk - 1) / kchunk);
-    kct::count_kernel<VARIANT><<<grid, threads, 0, st>>>(p->d_views, G, kchunk, p->d_count, p->d_err);
+    kct::count_kernel<VARIANT><<<column_grid(p->grid, p->grid.nviews), 32 * kct::WARPS, 0, st>>>(
+        p->d_views, p->grid, p->d_count, p->d_err);
 }
 
 kct_status check_plan(const kct_plan* p) {
@@ -249,6 +263,7 @@ kct_status kct_plan_create(kct_plan** out, const kct_volume_desc* vol, const kct
     p->d_views = nullptr;
     p->d_err = nullptr;
     p->d_count = nullptr;
+    p->d_work = nullptr;
     p->h_views.resize(nviews);
     for (int q = 0; q < nviews; ++q) {
         std::string why = setup_view(pmats + 12 * q, *vol, p->h_views[q]);
@@ -256,7 +271,8 @@ kct_status kct_plan_create(kct_plan** out, const kct_volume_desc* vol, const kct
             delete p;
             char buf[64];
             std::snprintf(buf, sizeof buf, "view %d: ", q);
-            return fail(KCT_ERR_GEOMETRY, buf + why);
+            bool unsup = why.compare(0, 12, "unsupported:") == 0;
+            return fail(unsup ? KCT_ERR_UNSUPPORTED : KCT_ERR_GEOMETRY, buf + why);
         }
     }
     Grid& G = p->grid;
@@ -273,16 +289,19 @@ kct_status kct_plan_create(kct_plan** out, const kct_volume_desc* vol, const kct
     if (e != cudaSuccess) { delete p; return fail(KCT_ERR_OOM, std::string("cudaMalloc views: ") + cudaGetErrorString(e)); }
     e = cudaMalloc(&p->d_err, sizeof(int) * 4);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_count, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_work, sizeof(float) * (size_t)npix);
     if (e != cudaSuccess) {
         cudaFree(p->d_views);
         cudaFree(p->d_err);
+        cudaFree(p->d_count);
+        cudaFree(p->d_work);
         delete p;
         return fail(KCT_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
     }
     e = cudaMemcpy(p->d_views, p->h_views.data(), sizeof(View) * nviews, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int) * 4);
     if (e != cudaSuccess) {
-        cudaFree(p->d_views); cudaFree(p->d_err); cudaFree(p->d_count);
+        cudaFree(p->d_views); cudaFree(p->d_err); cudaFree(p->d_count); cudaFree(p->d_work);
         delete p;
         return cuda_fail(e, "uploading view parameters");
     }
@@ -298,6 +317,7 @@ kct_status kct_plan_destroy(kct_plan* p) {
     cudaFree(p->d_views);
     cudaFree(p->d_err);
     cudaFree(p->d_count);
+    cudaFree(p->d_work);
     if (cur >= 0 && cur != p->device) cudaSetDevice(cur);
     delete p;
     return KCT_OK;
@@ -311,20 +331,15 @@ kct_status kct_project(const kct_plan* p, const float* d_vol, float* d_proj, int
     cudaStream_t st = (cudaStream_t)stream;
     const Grid& G = p->grid;
     size_t pbytes = sizeof(float) * (size_t)G.nu * G.nv * G.nviews;
-    cudaError_t e;
-    if (!accumulate) {
-        e = cudaMemsetAsync(d_proj, 0, pbytes, st);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    }
-    int key = (p->variant == KCT_CVP_RELAXED ? 2 : 0) + (p->scaling == KCT_SCALE_EXACT ? 1 : 0);
-    switch (key) {
-        case 0: launch_fwd<0, 0>(p, d_vol, d_proj, st); break;
-        case 1: launch_fwd<0, 1>(p, d_vol, d_proj, st); break;
-        case 2: launch_fwd<1, 0>(p, d_vol, d_proj, st); break;
-        default: launch_fwd<1, 1>(p, d_vol, d_proj, st); break;
-    }
+    cudaError_t e = cudaMemsetAsync(p->d_work, 0, pbytes, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    if (p->variant == KCT_CVP_RELAXED) launch_fwd<1>(p, d_vol, p->d_work, st);
+    else launch_fwd<0>(p, d_vol, p->d_work, st);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "forward projection launch");
+    launch_scale(p, p->d_work, d_proj, accumulate ? 1 : 0, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "pixel factor launch");
     return KCT_OK;
 }
 
@@ -334,15 +349,12 @@ kct_status kct_backproject(const kct_plan* p, const float* d_proj, float* d_vol,
     if (!d_vol || !d_proj) return fail(KCT_ERR_INVALID_ARG, "null data pointer");
     if ((s = set_device(p)) != KCT_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
-    int key = (p->variant == KCT_CVP_RELAXED ? 2 : 0) + (p->scaling == KCT_SCALE_EXACT ? 1 : 0);
-    int acc = accumulate ? 1 : 0;
-    switch (key) {
-        case 0: launch_bwd<0, 0>(p, d_proj, d_vol, acc, st); break;
-        case 1: launch_bwd<0, 1>(p, d_proj, d_vol, acc, st); break;
-        case 2: launch_bwd<1, 0>(p, d_proj, d_vol, acc, st); break;
-        default: launch_bwd<1, 1>(p, d_proj, d_vol, acc, st); break;
-    }
+    launch_scale(p, d_proj, p->d_work, 0, st);
     cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "pixel factor launch");
+    if (p->variant == KCT_CVP_RELAXED) launch_bwd<1>(p, p->d_work, d_vol, accumulate ? 1 : 0, st);
+    else launch_bwd<0>(p, p->d_work, d_vol, accumulate ? 1 : 0, st);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "backprojection launch");
     return KCT_OK;
 }
