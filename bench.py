@@ -1,0 +1,330 @@
+"""Benchmark of the cutting voxel projector on the 512^3 x 496-view cone-beam workload.
+
+One step = forward projection b = A x and backprojection x' = A^T y of both variants
+(near-exact and relaxed), i.e. every row of the hot path: per-view geometry is set up
+once at plan creation, then voxel footprints, column cuts, exact and relaxed row cuts,
+accumulation, pixel factors and the gather adjoint run inside each step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl kct|reference]
+
+Prints one JSON line (rank 0). `value` is whole-job voxel-views per second of P + BP:
+each step processes 2 * (512^3 * 496) voxel-view units (one P+BP per variant); N ranks
+run N independent replicas (the path needs no exchange between GPUs).
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "cvp512"
+METRIC = "CVP project+backproject Gvoxel·views/s at 512³×496 views; CGLS time-to-1e-3 residual"
+UNIT = "Gvoxel·views/s"
+
+# FP32 operations per voxel-view of the dominant (near-exact) kernels, counted by ncu
+# (thread-level executed FADD + FMUL + 2 * FFMA) on the 512^3 x 496 geometry and divided by
+# the voxel-views of the launch. None until measured.
+FLOP_PER_VV = {"exact project": None, "exact backproject": None}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="kct", choices=["kct", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--scaling", default="cos", choices=["cos", "exact"])
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [[p.strip() for p in line.split(",")] for line in open(self.path)]
+        rows = [r for r in rows if len(r) >= 9]
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = max((num(r[2]) for r in rows if num(r[2]) is not None), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in rows for q in range(4) if r[5 + q].lower() == "active"})
+        load = [v for v in sm if mx and v > 0.3 * mx] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_baseline(geom, seconds: float, seed: int = 5):
+    """The FP64 oracle's adjoint on randomly drawn voxels (all views), time-bounded.
+    Returns (voxel-views per second for P+BP, sample description, threads). The forward
+    projection clips the same voxel-pixel pairs, so one P+BP costs twice the adjoint."""
+    import numpy as np
+
+    import oracle
+    from paper_2110_09841_b300 import inputs
+
+    threads = oracle.num_threads()
+    y = inputs.uniform_projections(geom.proj_shape, seed).numpy()
+    rng = np.random.default_rng(seed)
+    done = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        vox = np.stack([rng.integers(0, geom.nz, threads), rng.integers(0, geom.ny, threads),
+                        rng.integers(0, geom.nx, threads)], axis=1)
+        oracle.backproject_voxels(geom, y, vox)
+        done += threads
+    dt = time.perf_counter() - t0
+    return (done * geom.nviews / dt / 2.0,
+            f"FP64 adjoint of {done} random voxels x {geom.nviews} views in {dt:.1f} s; P+BP = 2 x adjoint cost",
+            threads)
+
+
+WORKLOAD_DESC = ("cvp512: 512^3 voxels @ 0.25 mm, 496 views / 360 deg, SID 400 / SDD 600 mm, "
+                 "1232x960 detector @ 0.154 mm, seeded 40-ellipsoid phantom")
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2110_09841_b300 import inputs
+
+    geom = inputs.workload_geometry(args.workload)
+    for _ in range(args.warmup):
+        cpu_baseline(geom, 1.0)
+    vals, desc, threads = [], "", 1
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, desc, threads = cpu_baseline(geom, 5.0)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = statistics.mean(vals) / 1e9
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": WORKLOAD_DESC, "variant": "exact", "scaling": args.scaling},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_kct(args):
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2110_09841_b300 import build, inputs
+    from paper_2110_09841_b300.kct import Projector
+
+    build.build()
+    geom = inputs.workload_geometry(args.workload)
+    x = inputs.workload_phantom(args.workload, device=dev)
+    y = inputs.uniform_projections(geom.proj_shape, 2024, device=dev)
+    variants = ("exact", "relaxed")
+    ops = {v: Projector(geom, v, args.scaling) for v in variants}
+    b = {v: torch.empty(geom.proj_shape, dtype=torch.float32, device=dev) for v in variants}
+    xb = {v: torch.empty(geom.vol_shape, dtype=torch.float32, device=dev) for v in variants}
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        for v in variants:
+            if ev is not None:
+                ev[v][0].record(stream)
+            ops[v].project(x, out=b[v])
+            if ev is not None:
+                ev[v][1].record(stream)
+            ops[v].backproject(y, out=xb[v])
+            if ev is not None:
+                ev[v][2].record(stream)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    for v in variants:
+        assert ops[v].device_error() == 0, "device-side footprint check failed"
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    events = [{v: [torch.cuda.Event(enable_timing=True) for _ in range(3)] for v in variants}
+              for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    barrier()
+    t_start.record(stream)
+    for s in range(args.steps):
+        step(events[s])
+    t_end.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    per = {v: {"project_ms": statistics.median(e[v][0].elapsed_time(e[v][1]) for e in events),
+               "backproject_ms": statistics.median(e[v][1].elapsed_time(e[v][2]) for e in events)}
+           for v in variants}
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    units_per_step = 2 * geom.voxel_views          # one P+BP per variant
+    value = world * units_per_step * args.steps / (total_ms / 1e3) / 1e9
+    for v in variants:
+        p = per[v]
+        p["p_bp_gvv_s"] = geom.voxel_views / ((p["project_ms"] + p["backproject_ms"]) / 1e3) / 1e9
+        p["nnz_pairs"] = ops[v].count_pairs()
+
+    # end to end through the public API from pinned host buffers, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        xh = x.cpu().pin_memory()
+        yh = y.cpu().pin_memory()
+        bh = {v: torch.empty(geom.proj_shape, dtype=torch.float32).pin_memory() for v in variants}
+        xbh = {v: torch.empty(geom.vol_shape, dtype=torch.float32).pin_memory() for v in variants}
+        xd = torch.empty_like(x)
+        yd = torch.empty_like(y)
+
+        def e2e_step():
+            xd.copy_(xh, non_blocking=True)
+            yd.copy_(yh, non_blocking=True)
+            for v in variants:
+                ops[v].project(xd, out=b[v])
+                ops[v].backproject(yd, out=xb[v])
+                bh[v].copy_(b[v], non_blocking=True)
+                xbh[v].copy_(xb[v], non_blocking=True)
+
+        e2e_step()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        barrier()
+        ems = e0.elapsed_time(e1)
+        e2e = {"value": world * units_per_step * args.steps / (ems / 1e3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": (x.numel() + y.numel()) * 4,
+               "d2h_bytes_per_step": len(variants) * (x.numel() + y.numel()) * 4}
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel; the projector kernels are bound by FP32 ALU work
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    max_mhz = clocks.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2032.0)
+    peak_tflops = sms * 128 * 2 * max_mhz * 1e6 / 1e12
+    dom_v, dom_k = max(((v, k) for v in variants for k in ("project_ms", "backproject_ms")),
+                       key=lambda q: per[q[0]][q[1]])
+    dom_ms = per[dom_v][dom_k]
+    name = f"{dom_v} {dom_k[:-3]}"
+    flop_vv = FLOP_PER_VV.get(name)
+    achieved = (flop_vv * geom.voxel_views / (dom_ms / 1e3) / 1e12) if flop_vv else None
+    roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": (achieved / peak_tflops) if achieved else None, "traffic": None,
+                "peak_basis": f"FP32 FMA: {sms} SMs x 128 lanes x 2 FLOP x {max_mhz:.0f} MHz (derived)"}
+
+    cb_val, cb_desc, cb_threads = cpu_baseline(geom, 10.0)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (seeded ellipsoid phantom; U[0,1) projections for the adjoint)",
+           "config": {"workload": WORKLOAD_DESC,
+                      "step": "project + backproject, near-exact and relaxed variants",
+                      "scaling": args.scaling, "parallelism": f"replicas x{world}",
+                      "l2": "inputs (0.54 GB volume, 2.35 GB projections) larger than L2; no flush"},
+           "variants": per, "roofline": roofline,
+           "cpu_baseline": {"value": cb_val / 1e9, "unit": UNIT, "cores": cb_threads, "kind": "oracle",
+                            "sample": cb_desc},
+           "e2e": e2e, "gpu_launches": 8 * args.steps, "clocks": clocks}
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_kct(args)
+
+
+if __name__ == "__main__":
+    main()
