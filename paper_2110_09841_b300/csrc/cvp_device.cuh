@@ -17,16 +17,15 @@
 //   * the x_3 extent of a row over a base point depends on t' only (Eq.
 //     columnprojectionidentity and the row-plane pencil).
 //
-// Near-exact pair (exact variant). Let P_U = base square ∩ {u < U}, and for a row
-// boundary V let h_V(t') = clamp(p0 + p1 t', 0, a3) be the height of the part of the voxel
-// column above a base point that projects to v < V. Then
-//     G(U, V) = int_{P_U} (1, D.x') h_V dA      (volume and first moment along D)
-// is the 2D cumulative distribution of the voxel over the detector, and the cut of pixel
-// (n, m) follows by inclusion-exclusion of G at its four corners. G needs, for the
-// polygon P_U, the moments of weights 1, t', t'^2, lambda, lambda t' (lambda = t_c t' +
-// xi_c xi') over P_U ∩ {t' < tau} at the two depths tau where the row plane leaves the
-// voxel through its bottom and top faces. They are integrated exactly by Green's theorem
-// over the boundary of the convex polygon square ∩ {L1 < 0} ∩ {t' < tau}.
+// Near-exact pair (exact variant). H_n is clipped directly between the two column lines.
+// For a row boundary V, h_V(t') = clamp(p0 + p1 t', 0, a3) is the height of the part of the
+// voxel column above base point t' that projects to v < V. The cut of pixel (n, m) is
+//     int_{H_n} (h_{m+1/2} - h_{m-1/2}) (1, D.x') dA     (volume and first moment along D).
+// When both planes stay inside the voxel over the base the integrand is linear in t' and
+// the pair is a closed form of the moments of H_n (weights 1, t', t'^2, lambda, lambda t',
+// lambda = t_c t' + xi_c xi'). A plane that leaves the voxel through a face needs the
+// moments of H_n ∩ {t' < tau}; all polygon moments are exact Green's-theorem sums over
+// the boundary of the convex polygon base ∩ half-planes.
 // The weight is W = V / |c - s|^2 with c the centre of mass of the cut:
 //     |c - s|^2 = |D + M/V|^2 ~ (V |D|^2 + 2 D.M) / V       (D = x_vox - s),
 // the dropped |M/V|^2 / |D|^2 <= 3/4 (a / r)^2 being below the FP32 resolution of r^2 for
@@ -153,56 +152,64 @@ __device__ __forceinline__ void seg_part(Mom5& m, float pt, float px, float qt, 
     }
 }
 
-// Green sums of  square ∩ {L1 < 0} ∩ {t' < tau},  L1 = l1t t' + l1x xi' - l1c.
+// A half-plane {at t' + ax xi' - c < 0} of the (t', xi') plane. Line{0, 0, 1} is the
+// whole plane (inactive).
+struct Line {
+    float at, ax, c;
+};
+
+__device__ __forceinline__ Line line_none() { return Line{0.f, 0.f, 1.f}; }
+
+__device__ __forceinline__ float line_eval(const Line& l, float t, float x) { return fmaf(l.at, t, fmaf(l.ax, x, -l.c)); }
+
+// Green sums of  square ∩ H0 ∩ H1 ∩ H2  for three half-planes (any of them inactive).
 // The boundary of an intersection of convex sets is the union of each set's boundary
-// restricted to the others: square edges clipped by both half-planes, plus the segment of
-// each line inside the square clipped by the other half-plane, oriented counter-clockwise.
-template <bool USE1, bool USE2, bool FULL>
-__device__ __forceinline__ Mom5 region(const View& V, float l1t, float l1x, float l1c, float tau) {
+// restricted to the others: the square's edges clipped by the three half-planes, plus, for
+// each line, its chord through the square (from the point where the counter-clockwise
+// boundary leaves the half-plane to where it re-enters) clipped by the other two.
+template <bool FULL>
+__device__ __forceinline__ Mom5 region3(const View& V, const Line& l0, const Line& l1, const Line& l2) {
     Mom5 m = mom_zero();
-    float L1[4], L2[4];
+    float L[3][4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-        L1[e] = USE1 ? fmaf(l1t, V.sq_t[e], fmaf(l1x, V.sq_x[e], -l1c)) : -1.f;
-        L2[e] = USE2 ? V.sq_t[e] - tau : -1.f;
+        L[0][e] = line_eval(l0, V.sq_t[e], V.sq_x[e]);
+        L[1][e] = line_eval(l1, V.sq_t[e], V.sq_x[e]);
+        L[2][e] = line_eval(l2, V.sq_t[e], V.sq_x[e]);
     }
-    float x1t = 0.f, x1x = 0.f, n1t = 0.f, n1x = 0.f;   // exit / entry of line 1
-    float x2t = 0.f, x2x = 0.f, n2t = 0.f, n2x = 0.f;   // exit / entry of line 2
-    bool hx1 = false, hn1 = false, hx2 = false, hn2 = false;
+    float xt[3], xx[3], nt[3], nx[3];   // exit and entry points of each line's chord
+    bool hx[3], hn[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { xt[k] = xx[k] = nt[k] = nx[k] = 0.f; hx[k] = hn[k] = false; }
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
         const int f = (e + 1) & 3;
-        float pt = V.sq_t[e], px = V.sq_x[e], qt = V.sq_t[f], qx = V.sq_x[f];
+        const float pt = V.sq_t[e], px = V.sq_x[e], qt = V.sq_t[f], qx = V.sq_x[f];
         float s0 = 0.f, s1 = 1.f;
-        if (USE1) clip_param(L1[e], L1[f], s0, s1);
-        if (USE2) clip_param(L2[e], L2[f], s0, s1);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) clip_param(L[k][e], L[k][f], s0, s1);
         seg_part<FULL>(m, pt, px, qt, qx, s0, s1);
-        if (USE1) {
-            if ((L1[e] < 0.f) != (L1[f] < 0.f)) {
-                float ss = L1[e] / (L1[e] - L1[f]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if ((L[k][e] < 0.f) != (L[k][f] < 0.f)) {
+                float ss = L[k][e] / (L[k][e] - L[k][f]);
                 float ct = fmaf(ss, qt - pt, pt), cx = fmaf(ss, qx - px, px);
-                if (L1[e] < 0.f) { x1t = ct; x1x = cx; hx1 = true; }
-                else { n1t = ct; n1x = cx; hn1 = true; }
-            }
-        }
-        if (USE2) {
-            if ((L2[e] < 0.f) != (L2[f] < 0.f)) {
-                float ss = L2[e] / (L2[e] - L2[f]);
-                float ct = fmaf(ss, qt - pt, pt), cx = fmaf(ss, qx - px, px);
-                if (L2[e] < 0.f) { x2t = ct; x2x = cx; hx2 = true; }
-                else { n2t = ct; n2x = cx; hn2 = true; }
+                if (L[k][e] < 0.f) { xt[k] = ct; xx[k] = cx; hx[k] = true; }
+                else { nt[k] = ct; nx[k] = cx; hn[k] = true; }
             }
         }
     }
-    if (USE1 && hx1 && hn1) {     // along line 1 from its exit to its entry, inside {t' < tau}
-        float s0 = 0.f, s1 = 1.f;
-        if (USE2) clip_param(x1t - tau, n1t - tau, s0, s1);
-        seg_part<FULL>(m, x1t, x1x, n1t, n1x, s0, s1);
-    }
-    if (USE2 && hx2 && hn2) {     // along line 2 (t' = tau) inside {L1 < 0}
-        float s0 = 0.f, s1 = 1.f;
-        if (USE1) clip_param(fmaf(l1t, x2t, fmaf(l1x, x2x, -l1c)), fmaf(l1t, n2t, fmaf(l1x, n2x, -l1c)), s0, s1);
-        seg_part<FULL>(m, x2t, x2x, n2t, n2x, s0, s1);
+    const Line* ls[3] = {&l0, &l1, &l2};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (hx[k] && hn[k]) {
+            float s0 = 0.f, s1 = 1.f;
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                if (q != k)
+                    clip_param(line_eval(*ls[q], xt[k], xx[k]), line_eval(*ls[q], nt[k], nx[k]), s0, s1);
+            seg_part<FULL>(m, xt[k], xx[k], nt[k], nx[k], s0, s1);
+        }
     }
     return m;
 }
@@ -286,7 +293,7 @@ __device__ __forceinline__ void row_plane(const View& V, const Grid& G, const Co
 }
 
 // ----------------------------------------------------------------------------------------
-// Exact variant: enumerate (k, n, m, W) for voxels k0 <= k < k1 of column (i, j)
+// Column cuts and their moments
 // ----------------------------------------------------------------------------------------
 
 // normalised moments of a Green-sum record: 1, t', t'^2, lambda, lambda t'
@@ -310,16 +317,23 @@ __device__ __forceinline__ Mom mom_sub(const Mom& a, const Mom& b) {
     return Mom{a.m1 - b.m1, a.mt - b.mt, a.mtt - b.mtt, a.ml - b.ml, a.mlt - b.mlt};
 }
 
-enum { KIND_EMPTY = 0, KIND_GEN = 1, KIND_FULL = 2 };
+// The two boundary lines of detector column n on the voxel base: H_n = base ∩ lo ∩ hi with
+//   u > n - 1/2  (lo)  and  u < n + 1/2  (hi);   u < U  <=>  gu xi' + (cu - U) t' + tc (u_c - U) < 0.
+// A line that does not cut the base is made inactive.
+__device__ __forceinline__ void column_lines(const View& V, const Column& C, int n, Line& lo, Line& hi) {
+    const float Ul = (float)n - 0.5f, Uh = (float)n + 0.5f;
+    if (Ul > C.umin) lo = Line{-(V.cu - Ul) * C.itc, -C.gxi, fmaf(V.gu, C.alc, V.cu - Ul)};
+    else lo = line_none();
+    if (Uh < C.umax) hi = Line{(V.cu - Uh) * C.itc, C.gxi, -fmaf(V.gu, C.alc, V.cu - Uh)};
+    else hi = line_none();
+}
 
-// moments over P_c ∩ {t' < tau}
-__device__ __forceinline__ Mom cpm(const View& V, const Column& C, int kind, float l1t, float l1c,
-                                   const Mom& full, float tau) {
-    if (tau <= V.tmin_sq || kind == KIND_EMPTY) return Mom{0.f, 0.f, 0.f, 0.f, 0.f};
+// moments over H_n ∩ {t' < tau}
+__device__ __forceinline__ Mom cut_moments(const View& V, const Column& C, const Line& lo, const Line& hi,
+                                           const Mom& full, float tau) {
+    if (tau <= V.tmin_sq) return Mom{0.f, 0.f, 0.f, 0.f, 0.f};
     if (tau >= V.tmax_sq) return full;
-    Mom5 g = (kind == KIND_GEN) ? region<true, true, true>(V, l1t, C.gxi, l1c, tau)
-                                : region<false, true, true>(V, 0.f, 0.f, 0.f, tau);
-    return normalise(g, C.tc, C.xc);
+    return normalise(region3<true>(V, lo, hi, Line{1.f, 0.f, tau}), C.tc, C.xc);
 }
 
 }  // namespace kct

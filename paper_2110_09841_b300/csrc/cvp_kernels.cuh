@@ -2,16 +2,16 @@
 //
 // Work unit: one warp, one voxel column (i, j) of the volume, SEG = 32 * KPL consecutive
 // voxels along x_3 (lane l owns voxels kbase + l + 32 p, p < KPL), one view.
-//  * The column cuts of the voxel base are the same for every voxel of the column (Sec.
-//    III-A, Eq. columnprojectionidentity), so they are computed once per warp: lane c
-//    computes the polygon P_c = base ∩ {u < U_c} of column boundary c and the warp shares
-//    its moments with shuffles.
-//  * Each lane then walks the row boundaries of its own voxel. A row plane whose height
-//    stays inside the voxel over the whole base gives the cumulative cut in closed form
-//    from the polygon moments; a plane that leaves the voxel through its top or bottom
-//    face ("crossing") needs the moments of P_c cut at a depth tau. Crossing boundaries
-//    are queued per warp and evaluated by all 32 lanes together, one (event, column
-//    boundary) task per lane, so the clipping never runs with most of the warp idle.
+//  * The column cuts H_n of the voxel base are the same for every voxel of the column
+//    (Sec. III-A, Eq. columnprojectionidentity), so they are computed once per warp: lane c
+//    clips the base to detector column n = cstart + c and the warp shares the moments of
+//    H_n with shuffles.
+//  * Each lane then walks the rows of its own voxel. A row whose two planes stay inside the
+//    voxel over the whole base gives its pairs in closed form from the moments of H_n; a
+//    plane that leaves the voxel through its top or bottom face ("crossing") needs the
+//    moments of H_n cut at a depth tau. Crossing planes are queued per warp and evaluated
+//    by all 32 lanes together, one (event, column) task per lane, so the clipping never
+//    runs with most of the warp idle.
 // Forward projection and adjoint enumerate the same pairs with the same code, so
 // <A x, y> = <x, A^T y> holds to float rounding.
 #pragma once
@@ -22,75 +22,93 @@ namespace kct {
 
 constexpr int KPL = 2;             // voxels per lane in a column segment
 constexpr int SEG = 32 * KPL;      // voxels per warp segment
-constexpr int EV_CAP = 64;         // crossing boundaries queued per warp and round
+constexpr int EV_CAP = 64;         // crossing events queued per warp and round
 constexpr int KCT_ROWS = 32;       // row boundaries of one voxel (its footprint spans <= 31 rows)
 constexpr int WARPS = 4;           // warps per block (a 2 x 2 patch of columns)
 constexpr unsigned FULLMASK = 0xffffffffu;
 
 struct WarpSmem {
-    float fm[5][KCT_CB];           // moments of P_c: m1, mt, mtt, ml, mlt
+    float fm[5][KCT_CB];           // moments of H_n: m1, mt, mtt, ml, mlt
     float ev_p0[EV_CAP], ev_p1[EV_CAP], ev_zs[EV_CAP];
     float res_v[EV_CAP][KCT_CB];
     float res_q[EV_CAP][KCT_CB];
 };
 
-__device__ __forceinline__ int boundary_kind(float U, const Column& C) {
-    return (U <= C.umin) ? KIND_EMPTY : ((U >= C.umax) ? KIND_FULL : KIND_GEN);
+// Row-boundary classes (in the sense of the region v < V_b)
+enum { ROW_ZERO = 0, ROW_FULL = 1, ROW_LIN = 2, ROW_CROSS = 3 };
+
+// Height of {v < V_b} over base point t' is clamp(p0 + p1 t', 0, az), measured from the face
+// on which that region sits ("bottom frame"). The complementary region {v > V_b} has height
+// clamp(pt0 - p1 t', 0, az), pt0 = az - p0, measured from the opposite face ("top frame").
+struct RowPlane {
+    int cls;
+    float p0, p1, pt0;
+};
+
+__device__ __forceinline__ RowPlane row_boundary(const View& V, const Grid& G, const Column& C, const Slice& S,
+                                                 float Vb) {
+    RowPlane r;
+    r.p0 = r.p1 = 0.f;
+    r.pt0 = G.az;
+    if (Vb <= S.vmin) { r.cls = ROW_ZERO; return r; }
+    if (Vb >= S.vmax) { r.cls = ROW_FULL; r.p0 = G.az; r.pt0 = 0.f; return r; }
+    const float dv = -fmaf(V.gv, S.bc, V.cv - Vb);        // V_b - v_c
+    const float off = C.tc * dv * V.inv_agv;
+    r.p0 = 0.5f * G.az + off;
+    r.pt0 = 0.5f * G.az - off;
+    r.p1 = (Vb - V.cv) * V.inv_agv;
+    // does the plane leave the voxel through a horizontal face inside the base's depth range?
+    const float h_lo = fmaf(r.p1, V.tmin_sq, r.p0), h_hi = fmaf(r.p1, V.tmax_sq, r.p0);
+    r.cls = (fminf(h_lo, h_hi) < 0.f || fmaxf(h_lo, h_hi) > G.az) ? ROW_CROSS : ROW_LIN;
+    return r;
 }
 
-// Cumulative cut G(U_c, V_b) = (volume, first moment along D) for a crossing boundary:
-// h(t') = clamp(p0 + p1 t', 0, az) changes form at tau0 (h = 0) and tau1 (h = az).
-__device__ __forceinline__ void g_cross(const View& V, const Grid& G, const Column& C, int kind, float l1t,
-                                        float l1c, const Mom& full, float p0, float p1, float zs,
-                                        float& gv, float& gq) {
+// Volume and first moment along D of {(t', xi') in H_n, 0 < height < clamp(p0 + p1 t', 0, az)}
+// (height from the frame's face; zs = zeta_c * sign(gv), negated in the top frame),
+// for a plane that leaves the voxel through a face: h = 0 at tau0, h = az at tau1.
+__device__ __forceinline__ void g_cross(const View& V, const Grid& G, const Column& C, const Line& lo, const Line& hi,
+                                        const Mom& full, float p0, float p1, float zs, float& gv, float& gq) {
     const float az = G.az;
-    if (kind == KIND_EMPTY) { gv = 0.f; gq = 0.f; return; }
-    float p1s = (fabsf(p1) < 1e-30f) ? copysignf(1e-30f, p1) : p1;
-    float tau0 = -p0 / p1s, tau1 = (az - p0) / p1s;
-    Mom c0 = cpm(V, C, kind, l1t, l1c, full, tau0);
-    Mom c1 = cpm(V, C, kind, l1t, l1c, full, tau1);
+    const float p1s = (fabsf(p1) < 1e-30f) ? copysignf(1e-30f, p1) : p1;
+    const float tau0 = -p0 / p1s, tau1 = (az - p0) / p1s;
+    const Mom c0 = cut_moments(V, C, lo, hi, full, tau0);
+    const Mom c1 = cut_moments(V, C, lo, hi, full, tau1);
     Mom lin, fu;
     if (p1s > 0.f) { lin = mom_sub(c1, c0); fu = mom_sub(full, c1); }
     else { lin = mom_sub(c0, c1); fu = c1; }
-    float Vg = fmaf(p0, lin.m1, fmaf(p1, lin.mt, az * fu.m1));
-    float Sl = fmaf(p0, lin.ml, fmaf(p1, lin.mlt, az * fu.ml));
-    float Sh2 = fmaf(p0 * p0, lin.m1, fmaf(2.f * p0 * p1, lin.mt, fmaf(p1 * p1, lin.mtt, az * az * fu.m1)));
+    const float Vg = fmaf(p0, lin.m1, fmaf(p1, lin.mt, az * fu.m1));
+    const float Sl = fmaf(p0, lin.ml, fmaf(p1, lin.mlt, az * fu.ml));
+    const float Sh2 = fmaf(p0 * p0, lin.m1, fmaf(2.f * p0 * p1, lin.mt, fmaf(p1 * p1, lin.mtt, az * az * fu.m1)));
     gv = Vg;
     gq = fmaf(zs, fmaf(0.5f, Sh2, -0.5f * az * Vg), Sl);
 }
 
-// Row-boundary classes of the exact variant
-enum { ROW_ZERO = 0, ROW_FULL = 1, ROW_LIN = 2, ROW_CROSS = 3 };
-
-__device__ __forceinline__ int classify_row(const View& V, const Grid& G, const Column& C, const Slice& S,
-                                            float Vb, float& p0, float& p1) {
-    if (Vb <= S.vmin) return ROW_ZERO;
-    if (Vb >= S.vmax) return ROW_FULL;
-    row_plane(V, G, C, S, Vb, p0, p1);
-    // does the plane leave the voxel through a horizontal face inside the base's depth range?
-    float h_lo = fmaf(p1, V.tmin_sq, p0), h_hi = fmaf(p1, V.tmax_sq, p0);
-    float hmin = fminf(h_lo, h_hi), hmax = fmaxf(h_lo, h_hi);
-    return (hmin < 0.f || hmax > G.az) ? ROW_CROSS : ROW_LIN;
+// the same quantity for a plane that stays inside the voxel over the whole base
+__device__ __forceinline__ void g_lin(float az, float p0, float p1, float zs, float f1, float ft, float ftt, float fl,
+                                      float flt, float& gv, float& gq) {
+    const float Vg = fmaf(p0, f1, p1 * ft);
+    const float Sl = fmaf(p0, fl, p1 * flt);
+    const float Sh2 = fmaf(p0 * p0, f1, fmaf(2.f * p0 * p1, ft, p1 * p1 * ftt));
+    gv = Vg;
+    gq = fmaf(zs, fmaf(0.5f, Sh2, -0.5f * az * Vg), Sl);
 }
 
+// Near-exact pairs of one column segment. Columns n = cstart .. cstart + ncol - 1.
+// Each pair (n, m) is the integral over the column cut H_n of the height between the two
+// row planes of row m. When both planes stay inside the voxel this height is linear in t'
+// and the pair follows directly from the moments of H_n. Otherwise it is the difference of
+// the cut below the upper plane and the cut below the lower one, both measured from the
+// nearer face (bottom frame for the lower half of the voxel's rows, top frame for the upper
+// half), so that no pair is a small difference of two near-full voxel volumes.
 template <class Sink>
-__device__ __forceinline__ void exact_segment(const View& V, const Grid& G, const Column& C, int cstart, int nb,
+__device__ __forceinline__ void exact_segment(const View& V, const Grid& G, const Column& C, int cstart, int ncol,
                                               int kbase, int lane, WarpSmem* ws, Sink& sink, int* err) {
     const float az = G.az;
-    // moments of P_c for this lane's boundary c = lane, then shared
     Mom my = Mom{0.f, 0.f, 0.f, 0.f, 0.f};
-    if (lane < nb) {
-        float U = (float)(cstart + lane) - 0.5f;
-        int kind = boundary_kind(U, C);
-        if (kind == KIND_FULL) {
-            my.m1 = G.ax * G.ay;
-            my.mtt = V.sq_tt * (1.f / 12.f);
-            my.mlt = fmaf(C.tc, my.mtt, C.xc * (V.sq_tx * (1.f / 24.f)));
-        } else if (kind == KIND_GEN) {
-            float l1t = (V.cu - U) * C.itc;
-            float l1c = -fmaf(V.gu, C.alc, V.cu - U);
-            my = normalise(region<true, false, true>(V, l1t, C.gxi, l1c, 0.f), C.tc, C.xc);
-        }
+    if (lane < ncol) {
+        Line lo, hi;
+        column_lines(V, C, cstart + lane, lo, hi);
+        my = normalise(region3<true>(V, lo, hi, line_none()), C.tc, C.xc);
     }
     if (lane < KCT_CB) {
         ws->fm[0][lane] = my.m1;
@@ -109,20 +127,26 @@ __device__ __forceinline__ void exact_segment(const View& V, const Grid& G, cons
         flt[c] = __shfl_sync(FULLMASK, my.mlt, c);
     }
     __syncwarp();
+    const float dp0 = C.tc * V.inv_agv, dp1 = V.inv_agv;   // change of p0, p1 from one row boundary to the next
+    const float vtiny = 1e-9f * G.ax * G.ay * az;
 
     for (int pass = 0; pass < KPL; ++pass) {
         const int k = kbase + pass * 32 + lane;
         Slice S;
         bool act = (k < G.nz) && slice_setup(V, G, C, k, S);
         if (act && S.m_last - S.m_first + 2 > KCT_ROWS) { atomicOr(err, 1); act = false; }
-        const int R = act ? S.m_last - S.m_first + 1 : -1;
+        const int R = act ? S.m_last - S.m_first + 1 : 0;      // rows of this voxel
+        const int rb = (R + 1) >> 1;                            // rows r < rb use the bottom frame
         const float zs = act ? S.zc * V.sgv : 0.f;
-        // crossing boundaries of this lane's voxel (at most KCT_ROWS <= EV_CAP)
-        int nev = 0;
-        for (int b = 0; b <= R; ++b) {
-            float p0, p1;
-            if (classify_row(V, G, C, S, (float)(S.m_first + b) - 0.5f, p0, p1) == ROW_CROSS) ++nev;
-        }
+        // crossing boundaries: bottom-frame events for b <= rb, top-frame events for b >= rb
+        unsigned cross = 0u;
+        if (act)
+            for (int b = 0; b <= R; ++b)
+                if (row_boundary(V, G, C, S, (float)(S.m_first + b) - 0.5f).cls == ROW_CROSS) cross |= 1u << b;
+        const unsigned mbot = cross & ((2u << rb) - 1u);
+        const unsigned mtop = cross & ~((1u << rb) - 1u);
+        const int nbot = __popc(mbot);
+        const int nev = nbot + __popc(mtop);
         int incl = nev;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -130,37 +154,43 @@ __device__ __forceinline__ void exact_segment(const View& V, const Grid& G, cons
             if (lane >= o) incl += t;
         }
         const int base = incl - nev;
-        // lanes are served in contiguous groups whose events fit the queue
-        for (int lo = 0; lo < 32;) {
-            const int base_lo = __shfl_sync(FULLMASK, base, lo);
-            const unsigned fit = __ballot_sync(FULLMASK, lane >= lo && incl - base_lo <= EV_CAP);
-            const int hi = 32 - __clz(fit);
-            const bool mine = lane >= lo && lane < hi;
-            const int ne = __shfl_sync(FULLMASK, incl, hi - 1) - base_lo;
-            // 1) queue the group's crossing boundaries
-            if (mine) {
-                int e = base - base_lo;
+        // lanes are served in contiguous groups whose events fit the queue (a lane has at most
+        // KCT_ROWS + 1 <= EV_CAP events, so every group makes progress)
+        for (int lo_lane = 0; lo_lane < 32;) {
+            const int base_lo = __shfl_sync(FULLMASK, base, lo_lane);
+            const unsigned fit = __ballot_sync(FULLMASK, lane >= lo_lane && incl - base_lo <= EV_CAP);
+            const int hi_lane = 32 - __clz(fit);
+            const bool mine = lane >= lo_lane && lane < hi_lane;
+            const int ne = __shfl_sync(FULLMASK, incl, hi_lane - 1) - base_lo;
+            const int e0 = base - base_lo;
+            // 1) queue the group's crossing boundaries (frame-transformed plane parameters)
+            if (mine && nev) {
+                int e = e0;
                 for (int b = 0; b <= R; ++b) {
-                    float p0, p1;
-                    if (classify_row(V, G, C, S, (float)(S.m_first + b) - 0.5f, p0, p1) == ROW_CROSS) {
-                        ws->ev_p0[e] = p0;
-                        ws->ev_p1[e] = p1;
-                        ws->ev_zs[e] = zs;
-                        ++e;
+                    if (!((cross >> b) & 1u)) continue;
+                    const RowPlane rp = row_boundary(V, G, C, S, (float)(S.m_first + b) - 0.5f);
+                    if (b <= rb) {
+                        ws->ev_p0[e + __popc(mbot & ((1u << b) - 1u))] = rp.p0;
+                        ws->ev_p1[e + __popc(mbot & ((1u << b) - 1u))] = rp.p1;
+                        ws->ev_zs[e + __popc(mbot & ((1u << b) - 1u))] = zs;
+                    }
+                    if (b >= rb) {
+                        const int q = e + nbot + __popc(mtop & ((1u << b) - 1u));
+                        ws->ev_p0[q] = rp.pt0;
+                        ws->ev_p1[q] = -rp.p1;
+                        ws->ev_zs[q] = -zs;
                     }
                 }
             }
             __syncwarp();
-            // 2) the whole warp evaluates (event, column boundary) tasks
-            for (int t = lane; t < ne * nb; t += 32) {
-                const int e = t / nb, c = t - e * nb;
-                float U = (float)(cstart + c) - 0.5f;
-                float l1t = (V.cu - U) * C.itc;
-                float l1c = -fmaf(V.gu, C.alc, V.cu - U);
-                Mom full = Mom{ws->fm[0][c], ws->fm[1][c], ws->fm[2][c], ws->fm[3][c], ws->fm[4][c]};
+            // 2) the whole warp evaluates (event, column) tasks
+            for (int t = lane; t < ne * ncol; t += 32) {
+                const int e = t / ncol, c = t - e * ncol;
+                Line lo, hi;
+                column_lines(V, C, cstart + c, lo, hi);
+                const Mom full = Mom{ws->fm[0][c], ws->fm[1][c], ws->fm[2][c], ws->fm[3][c], ws->fm[4][c]};
                 float gv, gq;
-                g_cross(V, G, C, boundary_kind(U, C), l1t, l1c, full, ws->ev_p0[e], ws->ev_p1[e], ws->ev_zs[e],
-                        gv, gq);
+                g_cross(V, G, C, lo, hi, full, ws->ev_p0[e], ws->ev_p1[e], ws->ev_zs[e], gv, gq);
                 ws->res_v[e][c] = gv;
                 ws->res_q[e][c] = gq;
             }
@@ -169,87 +199,87 @@ __device__ __forceinline__ void exact_segment(const View& V, const Grid& G, cons
             if (mine && act) {
                 sink.begin(pass, k);
                 const float D2 = fmaf(C.tc, C.tc, fmaf(C.xc, C.xc, S.zc * S.zc));
-                const float vtiny = 1e-9f * G.ax * G.ay * az;
-                float pV[KCT_CB], pQ[KCT_CB];
-#pragma unroll
-                for (int c = 0; c < KCT_CB; ++c) { pV[c] = 0.f; pQ[c] = 0.f; }
-                int e = base - base_lo;
-                for (int b = 0; b <= R; ++b) {
-                    float p0 = 0.f, p1 = 0.f;
-                    const int cls = classify_row(V, G, C, S, (float)(S.m_first + b) - 0.5f, p0, p1);
-                    float gV[KCT_CB], gQ[KCT_CB];
-                    if (cls == ROW_ZERO) {
-#pragma unroll
-                        for (int c = 0; c < KCT_CB; ++c) { gV[c] = 0.f; gQ[c] = 0.f; }
-                    } else if (cls == ROW_FULL) {
-#pragma unroll
-                        for (int c = 0; c < KCT_CB; ++c) { gV[c] = az * f1[c]; gQ[c] = az * fl[c]; }
-                    } else if (cls == ROW_LIN) {
-                        const float p00 = p0 * p0, p01 = 2.f * p0 * p1, p11 = p1 * p1;
+                RowPlane rlo = row_boundary(V, G, C, S, (float)S.m_first - 0.5f);
+                for (int r = 0; r < R; ++r) {
+                    const int m = S.m_first + r;
+                    const RowPlane rhi = row_boundary(V, G, C, S, (float)m + 0.5f);
+                    float pv[KCT_CB], pq[KCT_CB];
+                    if (rlo.cls == ROW_LIN && rhi.cls == ROW_LIN) {
+                        // height between the planes: dp0 + dp1 t', centred at s0 + s1 t'
+                        const float s0 = C.tc * (-fmaf(V.gv, S.bc, V.cv - (float)m)) * V.inv_agv;
+                        const float s1 = ((float)m - V.cv) * V.inv_agv;
+                        const float a0 = zs * dp0 * s0, a1 = zs * fmaf(dp0, s1, dp1 * s0), a2 = zs * dp1 * s1;
 #pragma unroll
                         for (int c = 0; c < KCT_CB; ++c) {
-                            float Vg = fmaf(p0, f1[c], p1 * ft[c]);
-                            float Sl = fmaf(p0, fl[c], p1 * flt[c]);
-                            float Sh2 = fmaf(p00, f1[c], fmaf(p01, ft[c], p11 * ftt[c]));
-                            gV[c] = Vg;
-                            gQ[c] = fmaf(zs, fmaf(0.5f, Sh2, -0.5f * az * Vg), Sl);
+                            pv[c] = fmaf(dp0, f1[c], dp1 * ft[c]);
+                            pq[c] = fmaf(dp0, fl[c], fmaf(dp1, flt[c], fmaf(a0, f1[c], fmaf(a1, ft[c], a2 * ftt[c]))));
                         }
                     } else {
+                        const bool top = r >= rb;
+                        const int bl = r, bh = r + 1;
 #pragma unroll
-                        for (int c = 0; c < KCT_CB; ++c) { gV[c] = ws->res_v[e][c]; gQ[c] = ws->res_q[e][c]; }
-                        ++e;
-                    }
-                    if (b > 0) {
-                        const int m = S.m_first + b - 1;
-#pragma unroll
-                        for (int c = 0; c + 1 < KCT_CB; ++c) {
-                            if (c + 1 < nb) {
-                                float Vp = (gV[c + 1] - gV[c]) - (pV[c + 1] - pV[c]);
-                                float Qp = (gQ[c + 1] - gQ[c]) - (pQ[c + 1] - pQ[c]);
-                                if (Vp > vtiny) sink.pair(pass, cstart + c, m, Vp * Vp / fmaf(Vp, D2, 2.f * Qp));
+                        for (int c = 0; c < KCT_CB; ++c) {
+                            float gvl, gql, gvh, gqh;
+                            // lower plane
+                            if (rlo.cls == ROW_CROSS) {
+                                const int q = top ? e0 + nbot + __popc(mtop & ((1u << bl) - 1u))
+                                                  : e0 + __popc(mbot & ((1u << bl) - 1u));
+                                gvl = ws->res_v[q][c];
+                                gql = ws->res_q[q][c];
+                            } else if (top) {
+                                g_lin(az, rlo.pt0, -rlo.p1, -zs, f1[c], ft[c], ftt[c], fl[c], flt[c], gvl, gql);
+                            } else {
+                                g_lin(az, rlo.p0, rlo.p1, zs, f1[c], ft[c], ftt[c], fl[c], flt[c], gvl, gql);
                             }
+                            // upper plane
+                            if (rhi.cls == ROW_CROSS) {
+                                const int q = top ? e0 + nbot + __popc(mtop & ((1u << bh) - 1u))
+                                                  : e0 + __popc(mbot & ((1u << bh) - 1u));
+                                gvh = ws->res_v[q][c];
+                                gqh = ws->res_q[q][c];
+                            } else if (top) {
+                                g_lin(az, rhi.pt0, -rhi.p1, -zs, f1[c], ft[c], ftt[c], fl[c], flt[c], gvh, gqh);
+                            } else {
+                                g_lin(az, rhi.p0, rhi.p1, zs, f1[c], ft[c], ftt[c], fl[c], flt[c], gvh, gqh);
+                            }
+                            pv[c] = top ? gvl - gvh : gvh - gvl;
+                            pq[c] = top ? gql - gqh : gqh - gql;
                         }
                     }
 #pragma unroll
-                    for (int c = 0; c < KCT_CB; ++c) { pV[c] = gV[c]; pQ[c] = gQ[c]; }
+                    for (int c = 0; c < KCT_CB; ++c)
+                        if (c < ncol && pv[c] > vtiny) sink.pair(pass, cstart + c, m, pv[c] * pv[c] / fmaf(pv[c], D2, 2.f * pq[c]));
+                    rlo = rhi;
                 }
             }
             __syncwarp();
-            lo = hi;
+            lo_lane = hi_lane;
         }
     }
 }
 
+// Relaxed pairs: W = A_n d / |D|^2 with d the x_3 length of row m along the vertical line
+// through the centre of mass of H_n (Sec. III-A, Eq. cutvolume).
 template <class Sink>
-__device__ __forceinline__ void relaxed_segment(const View& V, const Grid& G, const Column& C, int cstart, int nb,
+__device__ __forceinline__ void relaxed_segment(const View& V, const Grid& G, const Column& C, int cstart, int ncol,
                                                 int kbase, int lane, Sink& sink, int* err) {
     const float az = G.az;
-    float A = 0.f, T = 0.f;       // area and t'-moment of P_c, c = lane
-    if (lane < nb) {
-        float U = (float)(cstart + lane) - 0.5f;
-        int kind = boundary_kind(U, C);
-        if (kind == KIND_FULL) A = G.ax * G.ay;
-        else if (kind == KIND_GEN) {
-            float l1t = (V.cu - U) * C.itc;
-            float l1c = -fmaf(V.gu, C.alc, V.cu - U);
-            Mom5 g = region<true, false, false>(V, l1t, C.gxi, l1c, 0.f);
-            A = 0.5f * g.a;
-            T = g.t * (1.f / 6.f);
-        }
+    float A = 0.f, T = 0.f;       // area and centre-of-mass depth of H_n, n = cstart + lane
+    if (lane < ncol) {
+        Line lo, hi;
+        column_lines(V, C, cstart + lane, lo, hi);
+        Mom5 g = region3<false>(V, lo, hi, line_none());
+        A = 0.5f * g.a;
+        T = (A > 0.f) ? g.t * (1.f / 6.f) / A : 0.f;
     }
-    float An[KCT_CB - 1], Tn[KCT_CB - 1];    // area and centre-of-mass depth of H_n
-    {
-        float Ap = __shfl_sync(FULLMASK, A, 0), Tp = __shfl_sync(FULLMASK, T, 0);
+    float An[KCT_CB], Tn[KCT_CB];
 #pragma unroll
-        for (int c = 0; c + 1 < KCT_CB; ++c) {
-            float Aq = __shfl_sync(FULLMASK, A, c + 1), Tq = __shfl_sync(FULLMASK, T, c + 1);
-            An[c] = Aq - Ap;
-            Tn[c] = (An[c] > 0.f) ? (Tq - Tp) / An[c] : 0.f;
-            Ap = Aq;
-            Tp = Tq;
-        }
+    for (int c = 0; c < KCT_CB; ++c) {
+        An[c] = __shfl_sync(FULLMASK, A, c);
+        Tn[c] = __shfl_sync(FULLMASK, T, c);
     }
     const float atiny = 1e-9f * G.ax * G.ay;
+    const float dp0 = C.tc * V.inv_agv, dp1 = V.inv_agv;
     for (int pass = 0; pass < KPL; ++pass) {
         const int k = kbase + pass * 32 + lane;
         Slice S;
@@ -258,22 +288,24 @@ __device__ __forceinline__ void relaxed_segment(const View& V, const Grid& G, co
         if (!act) continue;
         sink.begin(pass, k);
         const float iD2 = 1.0f / fmaf(C.tc, C.tc, fmaf(C.xc, C.xc, S.zc * S.zc));
-        float ph[KCT_CB - 1];
-#pragma unroll
-        for (int c = 0; c + 1 < KCT_CB; ++c) ph[c] = 0.f;
         const int R = S.m_last - S.m_first + 1;
-        for (int b = 0; b <= R; ++b) {
-            float p0, p1;
-            row_plane(V, G, C, S, (float)(S.m_first + b) - 0.5f, p0, p1);
+        const int rb = (R + 1) >> 1;
+        RowPlane rlo = row_boundary(V, G, C, S, (float)S.m_first - 0.5f);
+        for (int r = 0; r < R; ++r) {
+            const int m = S.m_first + r;
+            const RowPlane rhi = row_boundary(V, G, C, S, (float)m + 0.5f);
+            const bool top = r >= rb;
 #pragma unroll
-            for (int c = 0; c + 1 < KCT_CB; ++c) {
-                float h = fminf(fmaxf(fmaf(p1, Tn[c], p0), 0.f), az);
-                if (b > 0 && c + 1 < nb && An[c] > atiny) {
-                    float d = h - ph[c];
-                    if (d > 0.f) sink.pair(pass, cstart + c, S.m_first + b - 1, An[c] * d * iD2);
-                }
-                ph[c] = h;
+            for (int c = 0; c < KCT_CB; ++c) {
+                const float hl = fmaf(rlo.p1, Tn[c], rlo.p0), hh = fmaf(rhi.p1, Tn[c], rhi.p0);
+                float d;
+                if (hl > 0.f && hl < az && hh > 0.f && hh < az) d = fmaf(dp1, Tn[c], dp0);
+                else if (top) d = fminf(fmaxf(fmaf(-rlo.p1, Tn[c], rlo.pt0), 0.f), az) -
+                                  fminf(fmaxf(fmaf(-rhi.p1, Tn[c], rhi.pt0), 0.f), az);
+                else d = fminf(fmaxf(hh, 0.f), az) - fminf(fmaxf(hl, 0.f), az);
+                if (c < ncol && An[c] > atiny && d > 0.f) sink.pair(pass, cstart + c, m, An[c] * d * iD2);
             }
+            rlo = rhi;
         }
     }
 }
@@ -289,10 +321,10 @@ __device__ __forceinline__ void warp_column(const View& V, const Grid& G, int i,
         if (lane == 0) atomicOr(err, 1);
         return;
     }
-    for (int cstart = C.n_first; cstart <= C.n_last; cstart += KCT_CB - 1) {
-        const int nb = min(KCT_CB - 1, C.n_last - cstart + 1) + 1;
-        if (VARIANT == 1) relaxed_segment(V, G, C, cstart, nb, kbase, lane, sink, err);
-        else exact_segment(V, G, C, cstart, nb, kbase, lane, ws, sink, err);
+    for (int cstart = C.n_first; cstart <= C.n_last; cstart += KCT_CB) {
+        const int ncol = min(KCT_CB, C.n_last - cstart + 1);
+        if (VARIANT == 1) relaxed_segment(V, G, C, cstart, ncol, kbase, lane, sink, err);
+        else exact_segment(V, G, C, cstart, ncol, kbase, lane, ws, sink, err);
     }
 }
 
