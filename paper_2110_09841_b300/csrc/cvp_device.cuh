@@ -35,7 +35,11 @@
 // mass, d = h_{m+1/2}(t'_CM) - h_{m-1/2}(t'_CM), W = A_n d / |D|^2.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
+
+// geometry functions compile for host and device (the host copy serves debugging tools)
+#define KCT_HD __host__ __device__ __forceinline__
 
 namespace kct {
 
@@ -70,7 +74,7 @@ constexpr int KCT_MAX_SPAN = 4096;   // larger footprints are reported as errors
 // ----------------------------------------------------------------------------------------
 
 // Eq. cvp at the pixel centre: f^2 / (a cos^3 theta) = |gu gv| (1 + alpha^2 + beta^2)^{3/2}
-__device__ __forceinline__ float factor_cos(const View& V, int n, int m) {
+KCT_HD float factor_cos(const View& V, int n, int m) {
     float al = ((float)n - V.cu) * V.igu;
     float be = ((float)m - V.cv) * V.igv;
     float q = fmaf(al, al, fmaf(be, be, 1.0f));
@@ -82,7 +86,7 @@ __device__ __forceinline__ float factor_cos(const View& V, int n, int m) {
 // (P00, P10, P11), (P00, P11, P01) of the Van Oosterom-Strackee expression
 // tan(Omega/2) = |[a b c]| / (|a||b||c| + (a.b)|c| + (a.c)|b| + (b.c)|a|), where the
 // triple product of either triangle equals (a1 - a0)(b1 - b0) exactly.
-__device__ __forceinline__ float factor_exact(const View& V, int n, int m) {
+KCT_HD float factor_exact(const View& V, int n, int m) {
     float a0 = ((float)n - 0.5f - V.cu) * V.igu, a1 = ((float)n + 0.5f - V.cu) * V.igu;
     float b0 = ((float)m - 0.5f - V.cv) * V.igv, b1 = ((float)m + 0.5f - V.cv) * V.igv;
     float num = fabsf(V.igu * V.igv);
@@ -102,7 +106,7 @@ __device__ __forceinline__ float factor_exact(const View& V, int n, int m) {
 }
 
 template <int SCALING>
-__device__ __forceinline__ float pixel_factor(const View& V, int n, int m) {
+KCT_HD float pixel_factor(const View& V, int n, int m) {
     if (SCALING == 1) return factor_exact(V, n, m);
     return factor_cos(V, n, m);
 }
@@ -115,10 +119,10 @@ struct Mom5 {
     float a, t, x, tt, tx;   // sums of c, c(t0+t1), c(x0+x1), c(t0^2+t0 t1+t1^2), c(2t0x0+t0x1+t1x0+2t1x1)
 };
 
-__device__ __forceinline__ Mom5 mom_zero() { return Mom5{0.f, 0.f, 0.f, 0.f, 0.f}; }
+KCT_HD Mom5 mom_zero() { return Mom5{0.f, 0.f, 0.f, 0.f, 0.f}; }
 
 template <bool FULL>
-__device__ __forceinline__ void seg_acc(Mom5& m, float pt, float px, float qt, float qx) {
+KCT_HD void seg_acc(Mom5& m, float pt, float px, float qt, float qx) {
     float c = pt * qx - qt * px;
     m.a += c;
     m.t = fmaf(c, pt + qt, m.t);
@@ -130,7 +134,7 @@ __device__ __forceinline__ void seg_acc(Mom5& m, float pt, float px, float qt, f
 }
 
 // restrict the parameter interval [s0, s1] of a segment to {L < 0}; L linear along it
-__device__ __forceinline__ void clip_param(float Lp, float Lq, float& s0, float& s1) {
+KCT_HD void clip_param(float Lp, float Lq, float& s0, float& s1) {
     bool pin = Lp < 0.f, qin = Lq < 0.f;
     if (pin != qin) {
         float ss = Lp / (Lp - Lq);
@@ -143,7 +147,7 @@ __device__ __forceinline__ void clip_param(float Lp, float Lq, float& s0, float&
 
 // accumulate the part [s0, s1] of segment p -> q
 template <bool FULL>
-__device__ __forceinline__ void seg_part(Mom5& m, float pt, float px, float qt, float qx, float s0, float s1) {
+KCT_HD void seg_part(Mom5& m, float pt, float px, float qt, float qx, float s0, float s1) {
     if (s1 > s0) {
         float dt = qt - pt, dx = qx - px;
         float at = fmaf(s0, dt, pt), ax = fmaf(s0, dx, px);
@@ -158,9 +162,9 @@ struct Line {
     float at, ax, c;
 };
 
-__device__ __forceinline__ Line line_none() { return Line{0.f, 0.f, 1.f}; }
+KCT_HD Line line_none() { return Line{0.f, 0.f, 1.f}; }
 
-__device__ __forceinline__ float line_eval(const Line& l, float t, float x) { return fmaf(l.at, t, fmaf(l.ax, x, -l.c)); }
+KCT_HD float line_eval(const Line& l, float t, float x) { return fmaf(l.at, t, fmaf(l.ax, x, -l.c)); }
 
 // Green sums of  square ∩ H0 ∩ H1 ∩ H2  for three half-planes (any of them inactive).
 // The boundary of an intersection of convex sets is the union of each set's boundary
@@ -168,7 +172,7 @@ __device__ __forceinline__ float line_eval(const Line& l, float t, float x) { re
 // each line, its chord through the square (from the point where the counter-clockwise
 // boundary leaves the half-plane to where it re-enters) clipped by the other two.
 template <bool FULL>
-__device__ __forceinline__ Mom5 region3(const View& V, const Line& l0, const Line& l1, const Line& l2) {
+KCT_HD Mom5 region3(const View& V, const Line& l0, const Line& l1, const Line& l2) {
     Mom5 m = mom_zero();
     float L[3][4];
 #pragma unroll
@@ -227,7 +231,7 @@ struct Column {
     int n_first, n_last; // detector columns touched (clipped), n_first > n_last if none
 };
 
-__device__ __forceinline__ bool column_setup(const View& V, const Grid& G, int i, int j, Column& C) {
+KCT_HD bool column_setup(const View& V, const Grid& G, int i, int j, Column& C) {
     float x = fmaf((float)i, G.ax, G.x0);
     float y = fmaf((float)j, G.ay, G.y0);
     // compensated t = w.x + aw and xi = h.x + ah with w = (wx, wy), h = (-wy, wx)
@@ -263,7 +267,7 @@ struct Slice {
     int m_first, m_last;
 };
 
-__device__ __forceinline__ bool slice_setup(const View& V, const Grid& G, const Column& C, int k, Slice& S) {
+KCT_HD bool slice_setup(const View& V, const Grid& G, const Column& C, int k, Slice& S) {
     float z = fmaf((float)k, G.az, G.z0);
     float zc = z - V.sz;
     S.zc = zc;
@@ -284,7 +288,7 @@ __device__ __forceinline__ bool slice_setup(const View& V, const Grid& G, const 
 
 // Row boundary V in the voxel: h(t') = clamp(p0 + p1 t', 0, az) is the height of the part
 // of the column above base point t' that projects to v < V.
-__device__ __forceinline__ void row_plane(const View& V, const Grid& G, const Column& C, const Slice& S,
+KCT_HD void row_plane(const View& V, const Grid& G, const Column& C, const Slice& S,
                                           float Vb, float& p0, float& p1) {
     // V - v_c with v_c = cv + gv beta_c, evaluated as one fused operation
     float dv = -fmaf(V.gv, S.bc, V.cv - Vb);
@@ -301,7 +305,7 @@ struct Mom {
     float m1, mt, mtt, ml, mlt;
 };
 
-__device__ __forceinline__ Mom normalise(const Mom5& g, float tc, float xc) {
+KCT_HD Mom normalise(const Mom5& g, float tc, float xc) {
     Mom r;
     r.m1 = 0.5f * g.a;
     r.mt = g.t * (1.f / 6.f);
@@ -313,14 +317,14 @@ __device__ __forceinline__ Mom normalise(const Mom5& g, float tc, float xc) {
     return r;
 }
 
-__device__ __forceinline__ Mom mom_sub(const Mom& a, const Mom& b) {
+KCT_HD Mom mom_sub(const Mom& a, const Mom& b) {
     return Mom{a.m1 - b.m1, a.mt - b.mt, a.mtt - b.mtt, a.ml - b.ml, a.mlt - b.mlt};
 }
 
 // The two boundary lines of detector column n on the voxel base: H_n = base ∩ lo ∩ hi with
 //   u > n - 1/2  (lo)  and  u < n + 1/2  (hi);   u < U  <=>  gu xi' + (cu - U) t' + tc (u_c - U) < 0.
 // A line that does not cut the base is made inactive.
-__device__ __forceinline__ void column_lines(const View& V, const Column& C, int n, Line& lo, Line& hi) {
+KCT_HD void column_lines(const View& V, const Column& C, int n, Line& lo, Line& hi) {
     const float Ul = (float)n - 0.5f, Uh = (float)n + 0.5f;
     if (Ul > C.umin) lo = Line{-(V.cu - Ul) * C.itc, -C.gxi, fmaf(V.gu, C.alc, V.cu - Ul)};
     else lo = line_none();
@@ -329,7 +333,7 @@ __device__ __forceinline__ void column_lines(const View& V, const Column& C, int
 }
 
 // moments over H_n ∩ {t' < tau}
-__device__ __forceinline__ Mom cut_moments(const View& V, const Column& C, const Line& lo, const Line& hi,
+KCT_HD Mom cut_moments(const View& V, const Column& C, const Line& lo, const Line& hi,
                                            const Mom& full, float tau) {
     if (tau <= V.tmin_sq) return Mom{0.f, 0.f, 0.f, 0.f, 0.f};
     if (tau >= V.tmax_sq) return full;

@@ -45,7 +45,7 @@ struct RowPlane {
     float p0, p1, pt0;
 };
 
-__device__ __forceinline__ RowPlane row_boundary(const View& V, const Grid& G, const Column& C, const Slice& S,
+KCT_HD RowPlane row_boundary(const View& V, const Grid& G, const Column& C, const Slice& S,
                                                  float Vb) {
     RowPlane r;
     r.p0 = r.p1 = 0.f;
@@ -66,7 +66,7 @@ __device__ __forceinline__ RowPlane row_boundary(const View& V, const Grid& G, c
 // Volume and first moment along D of {(t', xi') in H_n, 0 < height < clamp(p0 + p1 t', 0, az)}
 // (height from the frame's face; zs = zeta_c * sign(gv), negated in the top frame),
 // for a plane that leaves the voxel through a face: h = 0 at tau0, h = az at tau1.
-__device__ __forceinline__ void g_cross(const View& V, const Grid& G, const Column& C, const Line& lo, const Line& hi,
+KCT_HD void g_cross(const View& V, const Grid& G, const Column& C, const Line& lo, const Line& hi,
                                         const Mom& full, float p0, float p1, float zs, float& gv, float& gq) {
     const float az = G.az;
     const float p1s = (fabsf(p1) < 1e-30f) ? copysignf(1e-30f, p1) : p1;
@@ -84,7 +84,7 @@ __device__ __forceinline__ void g_cross(const View& V, const Grid& G, const Colu
 }
 
 // the same quantity for a plane that stays inside the voxel over the whole base
-__device__ __forceinline__ void g_lin(float az, float p0, float p1, float zs, float f1, float ft, float ftt, float fl,
+KCT_HD void g_lin(float az, float p0, float p1, float zs, float f1, float ft, float ftt, float fl,
                                       float flt, float& gv, float& gq) {
     const float Vg = fmaf(p0, f1, p1 * ft);
     const float Sl = fmaf(p0, fl, p1 * flt);
@@ -199,10 +199,14 @@ __device__ __forceinline__ void exact_segment(const View& V, const Grid& G, cons
             if (mine && act) {
                 sink.begin(pass, k);
                 const float D2 = fmaf(C.tc, C.tc, fmaf(C.xc, C.xc, S.zc * S.zc));
+                // the crossing decision is taken once (the mask): a plane that touches a face
+                // to within rounding must not be classified differently here
                 RowPlane rlo = row_boundary(V, G, C, S, (float)S.m_first - 0.5f);
+                if (rlo.cls >= ROW_LIN) rlo.cls = (cross & 1u) ? ROW_CROSS : ROW_LIN;
                 for (int r = 0; r < R; ++r) {
                     const int m = S.m_first + r;
-                    const RowPlane rhi = row_boundary(V, G, C, S, (float)m + 0.5f);
+                    RowPlane rhi = row_boundary(V, G, C, S, (float)m + 0.5f);
+                    if (rhi.cls >= ROW_LIN) rhi.cls = ((cross >> (r + 1)) & 1u) ? ROW_CROSS : ROW_LIN;
                     float pv[KCT_CB], pq[KCT_CB];
                     if (rlo.cls == ROW_LIN && rhi.cls == ROW_LIN) {
                         // height between the planes: dp0 + dp1 t', centred at s0 + s1 t'
