@@ -161,23 +161,40 @@ std::string setup_view(const double* P, const kct_volume_desc& vol, View& V) {
     return std::string();
 }
 
-dim3 column_grid(const Grid& G, int third) {
-    const unsigned patches = (unsigned)(((G.nx + 1) / 2) * ((G.ny + 1) / 2));
-    return dim3(patches, (unsigned)third, (unsigned)((G.nz + kct::SEG - 1) / kct::SEG));
+unsigned bricks(const Grid& G) {
+    return (unsigned)(((G.nx + kct::BX - 1) / kct::BX) * ((G.ny + kct::BY - 1) / kct::BY));
+}
+
+unsigned segments(const Grid& G) { return (unsigned)((G.nz + kct::SEG - 1) / kct::SEG); }
+
+constexpr size_t kBrickDynSmem = sizeof(float) * (kct::SEG * kct::NCOLS + kct::TILE_CAP);
+
+// opt in to more than 48 KB of shared memory per block (once per process)
+cudaError_t brick_kernel_attributes() {
+    static cudaError_t done = [] {
+        cudaError_t e = cudaSuccess;
+        const int dyn = (int)kBrickDynSmem;
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(kct::fwd_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(kct::fwd_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(kct::bwd_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(kct::bwd_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        return e;
+    }();
+    return done;
 }
 
 template <int VARIANT>
 void launch_fwd(const kct_plan* p, const float* vol, float* S, cudaStream_t st) {
-    kct::fwd_kernel<VARIANT><<<column_grid(p->grid, p->grid.nviews), 32 * kct::WARPS, 0, st>>>(
-        p->d_views, p->grid, vol, S, p->d_err);
+    const Grid& G = p->grid;
+    dim3 grid(bricks(G), segments(G), (unsigned)((G.nviews + kct::VIEW_CHUNK - 1) / kct::VIEW_CHUNK));
+    kct::fwd_kernel<VARIANT><<<grid, kct::NTHREADS, kBrickDynSmem, st>>>(p->d_views, G, vol, S, p->d_err);
 }
 
 template <int VARIANT>
 void launch_bwd(const kct_plan* p, const float* yF, float* vol, int accumulate, cudaStream_t st) {
-    dim3 g = column_grid(p->grid, 1);
-    g.y = g.z;
-    g.z = 1;
-    kct::bwd_kernel<VARIANT><<<g, 32 * kct::WARPS, 0, st>>>(p->d_views, p->grid, yF, vol, accumulate, p->d_err);
+    const Grid& G = p->grid;
+    dim3 grid(bricks(G), segments(G));
+    kct::bwd_kernel<VARIANT><<<grid, kct::NTHREADS, kBrickDynSmem, st>>>(p->d_views, G, yF, vol, accumulate, p->d_err);
 }
 
 void launch_scale(const kct_plan* p, const float* in, float* out, int accumulate, cudaStream_t st) {
@@ -192,8 +209,9 @@ void launch_scale(const kct_plan* p, const float* in, float* out, int accumulate
 
 template <int VARIANT>
 void launch_count(const kct_plan* p, cudaStream_t st) {
-    kct::count_kernel<VARIANT><<<column_grid(p->grid, p->grid.nviews), 32 * kct::WARPS, 0, st>>>(
-        p->d_views, p->grid, p->d_count, p->d_err);
+    const Grid& G = p->grid;
+    dim3 grid(bricks(G), segments(G), (unsigned)G.nviews);
+    kct::count_kernel<VARIANT><<<grid, kct::NTHREADS, 0, st>>>(p->d_views, G, p->d_count, p->d_err);
 }
 
 kct_status check_plan(const kct_plan* p) {
@@ -285,6 +303,8 @@ kct_status kct_plan_create(kct_plan** out, const kct_volume_desc* vol, const kct
 
     cudaError_t e = cudaGetDevice(&p->device);
     if (e != cudaSuccess) { delete p; return cuda_fail(e, "cudaGetDevice"); }
+    e = brick_kernel_attributes();
+    if (e != cudaSuccess) { delete p; return cuda_fail(e, "cudaFuncSetAttribute"); }
     e = cudaMalloc(&p->d_views, sizeof(View) * nviews);
     if (e != cudaSuccess) { delete p; return fail(KCT_ERR_OOM, std::string("cudaMalloc views: ") + cudaGetErrorString(e)); }
     e = cudaMalloc(&p->d_err, sizeof(int) * 4);
