@@ -45,7 +45,41 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--scaling", default="cos", choices=["cos", "exact"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-case", default=None, metavar="WORKLOAD",
+                    help="run one projector call on a sub-sampled workload (for ncu captures) and exit")
+    ap.add_argument("--variant", default="exact", choices=["exact", "relaxed"])
+    ap.add_argument("--direction", default="fwd", choices=["fwd", "bwd"])
+    ap.add_argument("--views", type=int, default=32)
     return ap.parse_args()
+
+
+def run_profile_case(args):
+    """Two untimed calls and one timed call of one direction of one variant on the first
+    `--views` evenly spaced views of a workload: a small, self-contained case to capture
+    with ncu (`-s 2 -c 1` skips the untimed launches of the captured kernel)."""
+    import torch
+
+    from paper_2110_09841_b300 import inputs
+    from paper_2110_09841_b300.kct import Projector
+
+    g = inputs.workload_geometry(args.profile_case)
+    step = max(1, g.nviews // args.views)
+    g = g.subset_views(list(range(0, g.nviews, step))[:args.views])
+    x = inputs.workload_phantom(args.profile_case, device="cuda")
+    y = inputs.uniform_projections(g.proj_shape, 3, device="cuda")
+    A = Projector(g, args.variant, args.scaling)
+    call = (lambda: A.project(x)) if args.direction == "fwd" else (lambda: A.backproject(y))
+    call()
+    call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    call()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    print(json.dumps({"case": args.profile_case, "views": g.nviews, "variant": args.variant,
+                      "direction": args.direction, "ms": ms, "gvv_s": g.voxel_views / (ms / 1e3) / 1e9}))
 
 
 def dist_env():
@@ -320,7 +354,9 @@ def run_kct(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.profile_case:
+        run_profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_kct(args)
