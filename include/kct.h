@@ -143,6 +143,28 @@ kct_status kct_count_pairs(const kct_plan *plan, uint64_t *count, void *stream);
  * Nonzero codes: 1 = a voxel footprint larger than the kernel's bound was skipped. */
 kct_status kct_last_device_error(const kct_plan *plan, int32_t *code, void *stream);
 
+/*
+ * Forward projection for callers that must not allocate device memory (for example code
+ * running inside another framework's memory pool, or a runtime with no allocator, where a
+ * cudaMalloc would break the host application's memory accounting). The paper has no
+ * counterpart: this is the same operator as kct_project with the plan's geometry passed
+ * directly, and no plan.
+ *   vol, det, pmats, nviews, variant, scaling  as for kct_plan_create (pmats on the host);
+ *   d_vol, d_proj, accumulate, stream           as for kct_project.
+ * Its scratch (per-view parameters, the unscaled sums, an error word) is a fixed array of
+ * about 32.5 MiB compiled into the library, which every GPU that loads the library keeps
+ * until the process exits. Limits: nviews <= 4096 and nu * nv * nviews <= 8388608 pixels;
+ * larger requests return KCT_ERR_UNSUPPORTED before any work is enqueued.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * and must therefore come before any stream capture on that device. All calls share the
+ * one array and it keeps the last call's contents (cleared where needed at each call):
+ * calls that overlap on the GPU, on any streams, race and give wrong results.
+ * The per-view parameters are copied from a host stack buffer with cudaMemcpyAsync.
+ */
+kct_status kct_project_static(const kct_volume_desc *vol, const kct_detector_desc *det, const double *pmats,
+                              int32_t nviews, kct_variant variant, kct_scaling scaling, const float *d_vol,
+                              float *d_proj, int32_t accumulate, void *stream);
+
 /* Static description of a status code. */
 const char *kct_status_string(kct_status status);
 

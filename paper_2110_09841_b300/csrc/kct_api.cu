@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -432,3 +433,122 @@ kct_status kct_last_device_error(const kct_plan* p, int32_t* code, void* stream)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Forward projection without any allocation: scratch in a fixed device array
+// ---------------------------------------------------------------------------------------
+//
+// For callers that may not allocate device memory at all (code running inside another
+// library's memory pool or an allocator-free runtime, where every cudaMalloc would break the
+// host application's accounting). Layout of the array: per-view parameters, the error word,
+// the unscaled sums of every pixel.
+namespace {
+
+constexpr size_t kStaticViews = 4096;                     // views per call, at most
+constexpr size_t kStaticSums = size_t(8) << 20;           // pixels x views per call, at most
+constexpr size_t kStaticViewBytes = kStaticViews * sizeof(View);
+constexpr size_t kStaticErrOffset = kStaticViewBytes;
+constexpr size_t kStaticSumOffset = kStaticViewBytes + 256;
+constexpr size_t kStaticBytes = kStaticSumOffset + kStaticSums * sizeof(float);   // about 32.5 MiB
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+void* g_static_ptr[kMaxDevices];
+
+// Device address of g_static_scratch on the current device, looked up once per device.
+cudaError_t static_scratch(void** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_ptr[dev]) {
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_ptr[dev] = ptr;
+    }
+    *out = g_static_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" kct_status kct_project_static(const kct_volume_desc* vol, const kct_detector_desc* det,
+                                         const double* pmats, int32_t nviews, kct_variant variant,
+                                         kct_scaling scaling, const float* d_vol, float* d_proj,
+                                         int32_t accumulate, void* stream) {
+    g_last_error.clear();
+    if (!vol || !det || !pmats || !d_vol || !d_proj) return fail(KCT_ERR_INVALID_ARG, "null pointer argument");
+    if (vol->nx <= 0 || vol->ny <= 0 || vol->nz <= 0) return fail(KCT_ERR_INVALID_ARG, "volume sizes must be positive");
+    if (!(vol->ax > 0.0) || !(vol->ay > 0.0) || !(vol->az > 0.0) || !std::isfinite(vol->ax) ||
+        !std::isfinite(vol->ay) || !std::isfinite(vol->az))
+        return fail(KCT_ERR_INVALID_ARG, "voxel sizes must be positive and finite");
+    if (det->nu <= 0 || det->nv <= 0) return fail(KCT_ERR_INVALID_ARG, "detector sizes must be positive");
+    if (nviews <= 0) return fail(KCT_ERR_INVALID_ARG, "nviews must be positive");
+    if (variant != KCT_CVP_EXACT && variant != KCT_CVP_RELAXED) return fail(KCT_ERR_INVALID_ARG, "unknown variant");
+    if (scaling != KCT_SCALE_COS && scaling != KCT_SCALE_EXACT) return fail(KCT_ERR_INVALID_ARG, "unknown scaling");
+    const long long npix = (long long)det->nu * det->nv * nviews;
+    if ((size_t)nviews > kStaticViews)
+        return fail(KCT_ERR_UNSUPPORTED, "kct_project_static: more than 4096 views");
+    if ((size_t)npix > kStaticSums)
+        return fail(KCT_ERR_UNSUPPORTED, "kct_project_static: detector pixels x views exceed 8388608");
+    if ((long long)vol->nx * vol->ny * vol->nz > (1LL << 31) - 1)
+        return fail(KCT_ERR_UNSUPPORTED, "problem too large for 32-bit voxel indexing");
+
+    void* base = nullptr;
+    cudaError_t e = static_scratch(&base);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
+    e = brick_kernel_attributes();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    View* d_views = (View*)base;
+    int* d_err = (int*)((unsigned char*)base + kStaticErrOffset);
+    float* S = (float*)((unsigned char*)base + kStaticSumOffset);
+    cudaStream_t st = (cudaStream_t)stream;
+
+    // per-view parameters, converted on the host in small batches from a stack buffer
+    View batch[32];
+    for (int q0 = 0; q0 < nviews; q0 += 32) {
+        const int nb = (nviews - q0 < 32) ? nviews - q0 : 32;
+        for (int q = 0; q < nb; ++q) {
+            std::string why = setup_view(pmats + 12 * (size_t)(q0 + q), *vol, batch[q]);
+            if (!why.empty()) {
+                char buf[64];
+                std::snprintf(buf, sizeof buf, "view %d: ", q0 + q);
+                bool unsup = why.compare(0, 12, "unsupported:") == 0;
+                return fail(unsup ? KCT_ERR_UNSUPPORTED : KCT_ERR_GEOMETRY, buf + why);
+            }
+        }
+        // a pageable source is copied out before the call returns, so the batch can be reused
+        e = cudaMemcpyAsync(d_views + q0, batch, sizeof(View) * nb, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "uploading view parameters");
+    }
+    Grid G;
+    G.nx = vol->nx; G.ny = vol->ny; G.nz = vol->nz;
+    G.nu = det->nu; G.nv = det->nv; G.nviews = nviews;
+    G.ax = (float)vol->ax; G.ay = (float)vol->ay; G.az = (float)vol->az;
+    G.x0 = (float)(0.5 * (1 - vol->nx) * vol->ax);
+    G.y0 = (float)(0.5 * (1 - vol->ny) * vol->ay);
+    G.z0 = (float)(0.5 * (1 - vol->nz) * vol->az);
+    // the array keeps the previous call's contents: clear the sums and the error word
+    e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S, 0, sizeof(float) * (size_t)npix, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    dim3 grid(bricks(G), segments(G), (unsigned)((G.nviews + kct::VIEW_CHUNK - 1) / kct::VIEW_CHUNK));
+    if (variant == KCT_CVP_RELAXED)
+        kct::fwd_kernel<1><<<grid, kct::NTHREADS, kBrickDynSmem, st>>>(d_views, G, d_vol, S, d_err);
+    else
+        kct::fwd_kernel<0><<<grid, kct::NTHREADS, kBrickDynSmem, st>>>(d_views, G, d_vol, S, d_err);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "forward projection launch");
+    dim3 sgrid((unsigned)(((long)G.nu * G.nv + 255) / 256), G.nviews);
+    if (scaling == KCT_SCALE_EXACT)
+        kct::scale_kernel<1><<<sgrid, 256, 0, st>>>(d_views, G, S, d_proj, accumulate ? 1 : 0);
+    else
+        kct::scale_kernel<0><<<sgrid, 256, 0, st>>>(d_views, G, S, d_proj, accumulate ? 1 : 0);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "pixel factor launch");
+    return KCT_OK;
+}

@@ -24,7 +24,7 @@ STATUS = {0: "KCT_OK", 1: "KCT_ERR_INVALID_ARG", 2: "KCT_ERR_GEOMETRY", 3: "KCT_
 
 EXPORTED = ["kct_plan_create", "kct_plan_destroy", "kct_project", "kct_backproject",
             "kct_pixel_factors", "kct_count_pairs", "kct_last_device_error", "kct_status_string",
-            "kct_last_error_message", "kct_version"]
+            "kct_last_error_message", "kct_version", "kct_project_static"]
 
 
 class KctError(RuntimeError):
@@ -76,6 +76,9 @@ def load(path: str | None = None):
         lib.kct_last_error_message.restype = ctypes.c_char_p
         lib.kct_version.argtypes = []
         lib.kct_version.restype = I32
+        lib.kct_project_static.argtypes = [ctypes.POINTER(VolumeDesc), ctypes.POINTER(DetectorDesc), V, I32, I, I,
+                                           V, V, I32, V]
+        lib.kct_project_static.restype = I
         _lib = lib
     return _lib
 
