@@ -218,6 +218,66 @@ KCT_HD Mom5 region3(const View& V, const Line& l0, const Line& l1, const Line& l
     return m;
 }
 
+// Vertices (counter-clockwise) of the square clipped by two half-planes: each square edge
+// contributes its start vertex when inside both, then, in order along the edge, the points
+// where it crosses a line while inside the other half-plane. At most 8 points.
+KCT_HD int clip_square(const View& V, const Line& l0, const Line& l1, float* pt, float* px) {
+    int nv = 0;
+    for (int e = 0; e < 4; ++e) {
+        const int f = (e + 1) & 3;
+        const float at = V.sq_t[e], ax = V.sq_x[e], bt = V.sq_t[f], bx = V.sq_x[f];
+        const float A0 = line_eval(l0, at, ax), B0 = line_eval(l0, bt, bx);
+        const float A1 = line_eval(l1, at, ax), B1 = line_eval(l1, bt, bx);
+        if (A0 < 0.f && A1 < 0.f) { pt[nv] = at; px[nv] = ax; ++nv; }
+        // inside parameter intervals of the edge for each line
+        float a0 = 0.f, b0 = 1.f, a1 = 0.f, b1 = 1.f;
+        clip_param(A0, B0, a0, b0);
+        clip_param(A1, B1, a1, b1);
+        float s[2];
+        int ns = 0;
+        if ((A0 < 0.f) != (B0 < 0.f)) {
+            const float ss = A0 / (A0 - B0);
+            if (ss >= a1 && ss <= b1) s[ns++] = ss;
+        }
+        if ((A1 < 0.f) != (B1 < 0.f)) {
+            const float ss = A1 / (A1 - B1);
+            if (ss >= a0 && ss <= b0) s[ns++] = ss;
+        }
+        if (ns == 2 && s[1] < s[0]) { const float q = s[0]; s[0] = s[1]; s[1] = q; }
+        for (int q = 0; q < ns; ++q) {
+            pt[nv] = fmaf(s[q], bt - at, at);
+            px[nv] = fmaf(s[q], bx - ax, ax);
+            ++nv;
+        }
+    }
+    return nv;
+}
+
+// Green sums of  polygon ∩ {t' < tau}  for a convex polygon given by its vertices: the edges
+// clipped to the half-plane plus the chord along t' = tau from the exit to the entry point.
+template <bool FULL>
+KCT_HD Mom5 polygon_cut(const float* pt, const float* px, int nv, float tau) {
+    Mom5 m = mom_zero();
+    float xt = 0.f, xx = 0.f, nt = 0.f, nx = 0.f;
+    bool hx = false, hn = false;
+    for (int e = 0; e < nv; ++e) {
+        const int f = (e + 1 == nv) ? 0 : e + 1;
+        const float at = pt[e], ax = px[e], bt = pt[f], bx = px[f];
+        const float La = at - tau, Lb = bt - tau;
+        float s0 = 0.f, s1 = 1.f;
+        clip_param(La, Lb, s0, s1);
+        seg_part<FULL>(m, at, ax, bt, bx, s0, s1);
+        if ((La < 0.f) != (Lb < 0.f)) {
+            const float ss = La / (La - Lb);
+            const float ct = fmaf(ss, bt - at, at), cx = fmaf(ss, bx - ax, ax);
+            if (La < 0.f) { xt = ct; xx = cx; hx = true; }
+            else { nt = ct; nx = cx; hn = true; }
+        }
+    }
+    if (hx && hn) seg_acc<FULL>(m, xt, xx, nt, nx);
+    return m;
+}
+
 // ----------------------------------------------------------------------------------------
 // Column setup: the voxel column (i, j) in one view
 // ----------------------------------------------------------------------------------------

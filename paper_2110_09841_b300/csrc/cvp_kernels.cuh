@@ -40,11 +40,12 @@ constexpr unsigned FULLMASK = 0xffffffffu;
 
 struct WarpSmem {
     Column C;                      // the warp's current column
-    float4 fa[KCT_CB];             // moments of H_n: m1, mt, mtt, ml
-    float fb[KCT_CB];              // mlt
+    float pt[KCT_CB][8], px[KCT_CB][8];   // vertices of H_n, n = cstart + c
+    int nv[KCT_CB];
+    float4 fa[KCT_CB];             // exact: moments of H_n m1, mt, mtt, ml; relaxed: A_n, t_n, 1/t_n, -
+    float4 fb[KCT_CB];             // exact: mlt, t'-range of H_n (lo, hi), -
     float ev_p0[EV_CAP], ev_p1[EV_CAP], ev_zs[EV_CAP];
-    float res_v[EV_CAP][KCT_CB];
-    float res_q[EV_CAP][KCT_CB];
+    float res_v[EV_CAP], res_q[EV_CAP];
 };
 
 struct Tile {                      // detector window covered by a brick in one view
@@ -85,14 +86,11 @@ KCT_HD RowPlane row_boundary(const View& V, const Grid& G, const Column& C, cons
     return r;
 }
 
-// Moments (1, t', t'^2, lambda, lambda t') of H_n ∩ {t' < tau}; tau = +inf for all of H_n.
+// Moments (1, t', t'^2, lambda, lambda t') of H_n ∩ {t' < tau} from the vertices of H_n.
 // Not inlined: the polygon clipping exists once in the code and its callers stay small.
-__device__ __noinline__ Mom cut_moments_call(const View* V, const Column* C, int n, float tau) {
-    if (tau <= V->tmin_sq) return Mom{0.f, 0.f, 0.f, 0.f, 0.f};
-    Line lo, hi;
-    column_lines(*V, *C, n, lo, hi);
-    const Line lt = (tau < V->tmax_sq) ? Line{1.f, 0.f, tau} : line_none();
-    return normalise(region3<true>(*V, lo, hi, lt), C->tc, C->xc);
+__device__ __noinline__ Mom cut_moments_call(const float* pt, const float* px, int nv, float tau, float tc,
+                                             float xc) {
+    return normalise(polygon_cut<true>(pt, px, nv, tau), tc, xc);
 }
 
 // Volume and first moment along D of {(t', xi') in H_n, 0 < height < clamp(p0 + p1 t', 0, az)}
@@ -124,13 +122,14 @@ __device__ __forceinline__ float pair_weight(float pv, float pq, float D2) {
     return __fdividef(pv * pv, fmaf(pv, D2, 2.f * pq));
 }
 
-// Near-exact pairs of voxels kbase + lane + 32 p of the warp's column, columns
-// n = cstart .. cstart + ncol - 1. Each pair (n, m) is the integral over H_n of the height
-// between the two row planes of row m. When both planes stay inside the voxel this height
-// is linear in t' and the pair is a closed form of the moments of H_n. Otherwise it is the
-// difference of the cuts below (or above) the two planes, measured from the nearer face
-// (bottom frame for the lower half of the voxel's rows, top frame for the upper half), so
-// that no pair is a small difference of two near-full voxel volumes.
+// Near-exact pairs of voxels kbase + lane + 32 p of the warp's column with detector
+// columns n = cstart .. cstart + ncol - 1, one detector column at a time. Each pair (n, m)
+// is the integral over H_n of the height between the two row planes of row m. When both
+// planes stay inside the voxel over the depth range of H_n this height is linear in t'
+// and the pair is a closed form of the moments of H_n. Otherwise it is the difference of
+// the cuts below (or above) the two planes, measured from the nearer face (bottom frame
+// for the lower half of the rows, top frame for the upper half), so that no pair is a
+// small difference of two near-full voxel volumes.
 template <class Sink>
 __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const Column& C, int cstart, int ncol,
                                              int kbase, int lane, WarpSmem* ws, Sink& sink, int* err) {
@@ -139,164 +138,186 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
     const float vtiny = 1e-9f * G.ax * G.ay * az;
     for (int pass = 0; pass < KPL; ++pass) {
         const int k = kbase + pass * 32 + lane;
-        Slice S;
-        bool act = (k < G.nz) && slice_setup(V, G, C, k, S);
-        if (act && S.m_last - S.m_first + 2 > KCT_ROWS) { atomicOr(err, 1); act = false; }
-        const int R = act ? S.m_last - S.m_first + 1 : 0;      // rows of this voxel
-        const int rb = (R + 1) >> 1;                            // rows r < rb use the bottom frame
-        const float zs = act ? S.zc * V.sgv : 0.f;
-        // crossing boundaries: bottom-frame events for b <= rb, top-frame events for b >= rb
-        unsigned cross = 0u;
-        for (int b = 0; b <= R && act; ++b)
-            if (row_boundary(V, G, C, S, (float)(S.m_first + b) - 0.5f).cls == ROW_CROSS) cross |= 1u << b;
-        const unsigned mbot = cross & ((2u << rb) - 1u);
-        const unsigned mtop = cross & ~((1u << rb) - 1u);
-        const int nbot = __popc(mbot);
-        const int nev = nbot + __popc(mtop);
-        int incl = nev;
+        const bool act = k < G.nz;
+        const float zc = fmaf((float)k, az, G.z0) - V.sz;     // zeta of the voxel centre
+        const float bc = zc * C.itc;
+        const float zs = zc * V.sgv;
+        const float D2 = fmaf(C.tc, C.tc, fmaf(C.xc, C.xc, zc * zc));
+        if (act) sink.begin(pass, k);
+        for (int c = 0; c < ncol; ++c) {
+            const float4 fa = ws->fa[c], fb = ws->fb[c];
+            const float tlo = fb.y, thi = fb.z;
+            // rows touched by this voxel over the depth range of H_n
+            int m_first = 0, R = 0;
+            if (act && fa.x > 0.f) {
+                const float i0 = 1.0f / (C.tc + tlo), i1 = 1.0f / (C.tc + thi);
+                const float zl = zc - 0.5f * az, zh = zc + 0.5f * az;
+                const float b0 = fminf(fminf(zl * i0, zl * i1), fminf(zh * i0, zh * i1));
+                const float b1 = fmaxf(fmaxf(zl * i0, zl * i1), fmaxf(zh * i0, zh * i1));
+                const float va = fmaf(V.gv, b0, V.cv), vb = fmaf(V.gv, b1, V.cv);
+                m_first = max((int)floorf(fminf(va, vb) + 0.5f), 0);
+                const int m_last = min((int)floorf(fmaxf(va, vb) + 0.5f), G.nv - 1);
+                R = m_last - m_first + 1;
+                if (R + 1 > KCT_ROWS) { atomicOr(err, 1); R = 0; }
+                if (R < 0) R = 0;
+            }
+            const int rb = (R + 1) >> 1;                        // rows r < rb use the bottom frame
+            // height of {v < V_b} over t' is p0 + p1 t', p0 = az/2 + tc (V_b - v_c)/|gv|, p1 = (V_b - cv)/|gv|
+            const float off0 = C.tc * (-fmaf(V.gv, bc, V.cv - ((float)m_first - 0.5f))) * V.inv_agv;
+            const float p1_0 = ((float)m_first - 0.5f - V.cv) * V.inv_agv;
+            // classes of the boundaries: 0 / az for planes outside the voxel, crossing mask
+            unsigned cross = 0u, zero = 0u, full = 0u;
+            for (int b = 0; b <= R; ++b) {
+                const float p0 = fmaf(0.5f, az, fmaf((float)b, dp0, off0)), p1 = fmaf((float)b, dp1, p1_0);
+                const float h0 = fmaf(p1, tlo, p0), h1 = fmaf(p1, thi, p0);
+                const float hmin = fminf(h0, h1), hmax = fmaxf(h0, h1);
+                if (hmax <= 0.f) zero |= 1u << b;
+                else if (hmin >= az) full |= 1u << b;
+                else if (hmin < 0.f || hmax > az) cross |= 1u << b;
+            }
+            const unsigned mbot = cross & ((2u << rb) - 1u);
+            const unsigned mtop = cross & ~((1u << rb) - 1u);
+            const int nbot = __popc(mbot);
+            const int nev = nbot + __popc(mtop);
+            int base = 0, total = 0;
+            if (__any_sync(FULLMASK, nev > 0)) {
+                int incl = nev;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int t = __shfl_up_sync(FULLMASK, incl, o);
-            if (lane >= o) incl += t;
-        }
-        const int base = incl - nev;
-        // lanes are served in contiguous groups whose events fit the queue (a lane has at most
-        // KCT_ROWS + 1 <= EV_CAP events, so every group makes progress)
-        for (int lo_lane = 0; lo_lane < 32;) {
-            const int base_lo = __shfl_sync(FULLMASK, base, lo_lane);
-            const unsigned fit = __ballot_sync(FULLMASK, lane >= lo_lane && incl - base_lo <= EV_CAP);
-            const int hi_lane = 32 - __clz(fit);
-            const bool mine = lane >= lo_lane && lane < hi_lane;
-            const int ne = __shfl_sync(FULLMASK, incl, hi_lane - 1) - base_lo;
-            const int e0 = base - base_lo;
-            // 1) queue the group's crossing planes (frame-transformed parameters)
-            if (mine && nev) {
-                for (int b = 0; b <= R; ++b) {
-                    if (!((cross >> b) & 1u)) continue;
-                    const RowPlane rp = row_boundary(V, G, C, S, (float)(S.m_first + b) - 0.5f);
-                    if (b <= rb) {
-                        const int q = e0 + __popc(mbot & ((1u << b) - 1u));
-                        ws->ev_p0[q] = rp.p0;
-                        ws->ev_p1[q] = rp.p1;
-                        ws->ev_zs[q] = zs;
-                    }
-                    if (b >= rb) {
-                        const int q = e0 + nbot + __popc(mtop & ((1u << b) - 1u));
-                        ws->ev_p0[q] = rp.pt0;
-                        ws->ev_p1[q] = -rp.p1;
-                        ws->ev_zs[q] = -zs;
-                    }
+                for (int o = 1; o < 32; o <<= 1) {
+                    int t = __shfl_up_sync(FULLMASK, incl, o);
+                    if (lane >= o) incl += t;
                 }
+                base = incl - nev;
+                total = __shfl_sync(FULLMASK, incl, 31);
             }
-            __syncwarp();
-            // 2) the whole warp evaluates (event, column) tasks
-            for (int t = lane; t < ne * ncol; t += 32) {
-                const int e = t / ncol, c = t - e * ncol;
-                const float p0 = ws->ev_p0[e], p1 = ws->ev_p1[e];
-                const float p1s = (fabsf(p1) < 1e-30f) ? copysignf(1e-30f, p1) : p1;
-                const float4 a = ws->fa[c];
-                const Mom full = Mom{a.x, a.y, a.z, a.w, ws->fb[c]};
-                const Mom c0 = cut_moments_call(&V, &ws->C, cstart + c, -p0 / p1s);
-                const Mom c1 = cut_moments_call(&V, &ws->C, cstart + c, (az - p0) / p1s);
-                float gv, gq;
-                g_cross_from(az, c0, c1, full, p0, p1, p1s, ws->ev_zs[e], gv, gq);
-                ws->res_v[e][c] = gv;
-                ws->res_q[e][c] = gq;
-            }
-            __syncwarp();
-            // 3) pairs of the group's voxels
-            if (mine && act) {
-                sink.begin(pass, k);
-                const float D2 = fmaf(C.tc, C.tc, fmaf(C.xc, C.xc, S.zc * S.zc));
-                // the crossing decision is taken once (the mask): a plane that touches a face
-                // to within rounding must not be classified differently here
-                RowPlane rlo = row_boundary(V, G, C, S, (float)S.m_first - 0.5f);
-                if (rlo.cls >= ROW_LIN) rlo.cls = (cross & 1u) ? ROW_CROSS : ROW_LIN;
-                for (int r = 0; r < R; ++r) {
-                    const int m = S.m_first + r;
-                    RowPlane rhi = row_boundary(V, G, C, S, (float)m + 0.5f);
-                    if (rhi.cls >= ROW_LIN) rhi.cls = ((cross >> (r + 1)) & 1u) ? ROW_CROSS : ROW_LIN;
-                    if (rlo.cls == ROW_LIN && rhi.cls == ROW_LIN) {
-                        // height between the planes: dp0 + dp1 t', centred at s0 + s1 t'
-                        const float s0 = C.tc * (-fmaf(V.gv, S.bc, V.cv - (float)m)) * V.inv_agv;
-                        const float s1 = ((float)m - V.cv) * V.inv_agv;
-                        const float a0 = zs * dp0 * s0, a1 = zs * fmaf(dp0, s1, dp1 * s0), a2 = zs * dp1 * s1;
-#pragma unroll 1
-                        for (int c = 0; c < ncol; ++c) {
-                            const float4 f = ws->fa[c];
-                            const float pv = fmaf(dp0, f.x, dp1 * f.y);
-                            const float pq = fmaf(dp0, f.w, fmaf(dp1, ws->fb[c], fmaf(a0, f.x, fmaf(a1, f.y, a2 * f.z))));
-                            if (pv > vtiny) sink.pair(pass, cstart + c, m, pair_weight(pv, pq, D2));
-                        }
-                    } else {
-                        const bool top = r >= rb;
-                        const int ql = rlo.cls == ROW_CROSS ? (top ? e0 + nbot + __popc(mtop & ((1u << r) - 1u))
-                                                                   : e0 + __popc(mbot & ((1u << r) - 1u))) : -1;
-                        const int qh = rhi.cls == ROW_CROSS ? (top ? e0 + nbot + __popc(mtop & ((1u << (r + 1)) - 1u))
-                                                                   : e0 + __popc(mbot & ((1u << (r + 1)) - 1u))) : -1;
-                        const float lp0 = top ? rlo.pt0 : rlo.p0, lp1 = top ? -rlo.p1 : rlo.p1;
-                        const float hp0 = top ? rhi.pt0 : rhi.p0, hp1 = top ? -rhi.p1 : rhi.p1;
-                        const float fz = top ? -zs : zs;
-#pragma unroll 1
-                        for (int c = 0; c < ncol; ++c) {
-                            const float4 f = ws->fa[c];
-                            const float fb = ws->fb[c];
-                            float gvl, gql, gvh, gqh;
-                            if (ql >= 0) { gvl = ws->res_v[ql][c]; gql = ws->res_q[ql][c]; }
-                            else g_lin(az, lp0, lp1, fz, f.x, f.y, f.z, f.w, fb, gvl, gql);
-                            if (qh >= 0) { gvh = ws->res_v[qh][c]; gqh = ws->res_q[qh][c]; }
-                            else g_lin(az, hp0, hp1, fz, f.x, f.y, f.z, f.w, fb, gvh, gqh);
-                            const float pv = top ? gvl - gvh : gvh - gvl;
-                            const float pq = top ? gql - gqh : gqh - gql;
-                            if (pv > vtiny) sink.pair(pass, cstart + c, m, pair_weight(pv, pq, D2));
+            // lanes are served in contiguous groups whose events fit the queue (a lane has at
+            // most KCT_ROWS + 1 <= EV_CAP events, so every group makes progress)
+            for (int lo_lane = 0; lo_lane < 32;) {
+                int hi_lane = 32, e0 = 0;
+                if (total > 0) {
+                    const int incl = base + nev;
+                    const int base_lo = __shfl_sync(FULLMASK, base, lo_lane);
+                    const unsigned fit = __ballot_sync(FULLMASK, lane >= lo_lane && incl - base_lo <= EV_CAP);
+                    hi_lane = 32 - __clz(fit);
+                    const int ne = __shfl_sync(FULLMASK, incl, hi_lane - 1) - base_lo;
+                    e0 = base - base_lo;
+                    // 1) queue the group's crossing planes (frame-transformed parameters)
+                    if (lane >= lo_lane && lane < hi_lane && nev) {
+                        for (int b = 0; b <= R; ++b) {
+                            if (!((cross >> b) & 1u)) continue;
+                            const float p0 = fmaf(0.5f, az, fmaf((float)b, dp0, off0)), p1 = fmaf((float)b, dp1, p1_0);
+                            if (b <= rb) {
+                                const int q = e0 + __popc(mbot & ((1u << b) - 1u));
+                                ws->ev_p0[q] = p0;
+                                ws->ev_p1[q] = p1;
+                                ws->ev_zs[q] = zs;
+                            }
+                            if (b >= rb) {
+                                const int q = e0 + nbot + __popc(mtop & ((1u << b) - 1u));
+                                ws->ev_p0[q] = az - p0;
+                                ws->ev_p1[q] = -p1;
+                                ws->ev_zs[q] = -zs;
+                            }
                         }
                     }
-                    rlo = rhi;
+                    __syncwarp();
+                    // 2) the whole warp evaluates the events (cut moments at the crossing depths)
+                    for (int e = lane; e < ne; e += 32) {
+                        const float p0 = ws->ev_p0[e], p1 = ws->ev_p1[e];
+                        const float p1s = (fabsf(p1) < 1e-30f) ? copysignf(1e-30f, p1) : p1;
+                        const Mom full_m = Mom{fa.x, fa.y, fa.z, fa.w, fb.x};
+                        const float tau0 = -p0 / p1s, tau1 = (az - p0) / p1s;
+                        const Mom zero_m = Mom{0.f, 0.f, 0.f, 0.f, 0.f};
+                        const Mom c0 = (tau0 <= tlo) ? zero_m : (tau0 >= thi) ? full_m
+                                       : cut_moments_call(ws->pt[c], ws->px[c], ws->nv[c], tau0, C.tc, C.xc);
+                        const Mom c1 = (tau1 <= tlo) ? zero_m : (tau1 >= thi) ? full_m
+                                       : cut_moments_call(ws->pt[c], ws->px[c], ws->nv[c], tau1, C.tc, C.xc);
+                        float gv, gq;
+                        g_cross_from(az, c0, c1, full_m, p0, p1, p1s, ws->ev_zs[e], gv, gq);
+                        ws->res_v[e] = gv;
+                        ws->res_q[e] = gq;
+                    }
+                    __syncwarp();
                 }
-                sink.end(pass, k);
+                // 3) pairs of the group's voxels with detector column n
+                if (lane >= lo_lane && lane < hi_lane && R > 0) {
+                    const int n = cstart + c;
+                    for (int r = 0; r < R; ++r) {
+                        const int m = m_first + r;
+                        const unsigned bl = 1u << r, bh = 2u << r;
+                        float pv, pq;
+                        if (!((cross | zero | full) & (bl | bh))) {
+                            // both planes inside: height dp0 + dp1 t' centred at s0 + s1 t'
+                            const float s0 = C.tc * (-fmaf(V.gv, bc, V.cv - (float)m)) * V.inv_agv;
+                            const float s1 = ((float)m - V.cv) * V.inv_agv;
+                            const float a0 = zs * dp0 * s0, a1 = zs * fmaf(dp0, s1, dp1 * s0), a2 = zs * dp1 * s1;
+                            pv = fmaf(dp0, fa.x, dp1 * fa.y);
+                            pq = fmaf(dp0, fa.w, fmaf(dp1, fb.x, fmaf(a0, fa.x, fmaf(a1, fa.y, a2 * fa.z))));
+                        } else {
+                            const bool top = r >= rb;
+                            float g[2][2];
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const int b = r + h;
+                                const unsigned bit = 1u << b;
+                                float p0 = fmaf(0.5f, az, fmaf((float)b, dp0, off0)), p1 = fmaf((float)b, dp1, p1_0);
+                                if (zero & bit) { p0 = 0.f; p1 = 0.f; }
+                                if (full & bit) { p0 = az; p1 = 0.f; }
+                                if (cross & bit) {
+                                    const int q = top ? e0 + nbot + __popc(mtop & (bit - 1u)) : e0 + __popc(mbot & (bit - 1u));
+                                    g[h][0] = ws->res_v[q];
+                                    g[h][1] = ws->res_q[q];
+                                } else if (top) {
+                                    g_lin(az, az - p0, -p1, -zs, fa.x, fa.y, fa.z, fa.w, fb.x, g[h][0], g[h][1]);
+                                } else {
+                                    g_lin(az, p0, p1, zs, fa.x, fa.y, fa.z, fa.w, fb.x, g[h][0], g[h][1]);
+                                }
+                            }
+                            pv = top ? g[0][0] - g[1][0] : g[1][0] - g[0][0];
+                            pq = top ? g[0][1] - g[1][1] : g[1][1] - g[0][1];
+                        }
+                        if (pv > vtiny) sink.pair(pass, n, m, pair_weight(pv, pq, D2));
+                    }
+                }
+                if (total > 0) __syncwarp();
+                lo_lane = hi_lane;
             }
-            __syncwarp();
-            lo_lane = hi_lane;
         }
+        if (act) sink.end(pass, k);
     }
 }
 
 // Relaxed pairs: W = A_n d / |D|^2 with d the x_3 length of row m along the vertical line
-// through the centre of mass of H_n (Sec. III-A, Eq. cutvolume). fa[c] = (A_n, t'_CM, ., .).
+// through the centre of mass of H_n (Sec. III-A, Eq. cutvolume, voxel-centre r). At the
+// depth t_n = t_c + t'_CM of that line the voxel spans v_n -+ hv in detector rows, v_n =
+// cv + gv zeta_c / t_n, hv = |gv| az / (2 t_n), and d = (overlap with [m - 1/2, m + 1/2]) t_n / |gv|;
+// the overlap is evaluated relative to v_n so that no large row index enters a difference.
 template <class Sink>
 __device__ __forceinline__ void relaxed_voxels(const View& V, const Grid& G, const Column& C, int cstart, int ncol,
                                                int kbase, int lane, WarpSmem* ws, Sink& sink, int* err) {
     const float az = G.az;
-    const float atiny = 1e-9f * G.ax * G.ay;
-    const float dp0 = C.tc * V.inv_agv, dp1 = V.inv_agv;
     for (int pass = 0; pass < KPL; ++pass) {
         const int k = kbase + pass * 32 + lane;
-        Slice S;
-        bool act = (k < G.nz) && slice_setup(V, G, C, k, S);
-        if (act && S.m_last - S.m_first + 2 > KCT_ROWS) { atomicOr(err, 1); act = false; }
-        if (!act) continue;
+        if (k >= G.nz) continue;
         sink.begin(pass, k);
-        const float iD2 = 1.0f / fmaf(C.tc, C.tc, fmaf(C.xc, C.xc, S.zc * S.zc));
-        const int R = S.m_last - S.m_first + 1;
-        const int rb = (R + 1) >> 1;
-        RowPlane rlo = row_boundary(V, G, C, S, (float)S.m_first - 0.5f);
-        for (int r = 0; r < R; ++r) {
-            const int m = S.m_first + r;
-            const RowPlane rhi = row_boundary(V, G, C, S, (float)m + 0.5f);
-            const bool top = r >= rb;
-#pragma unroll 1
-            for (int c = 0; c < ncol; ++c) {
-                const float4 f = ws->fa[c];
-                const float A = f.x, T = f.y;
-                const float hl = fmaf(rlo.p1, T, rlo.p0), hh = fmaf(rhi.p1, T, rhi.p0);
-                float d;
-                if (hl > 0.f && hl < az && hh > 0.f && hh < az) d = fmaf(dp1, T, dp0);
-                else if (top) d = fminf(fmaxf(fmaf(-rlo.p1, T, rlo.pt0), 0.f), az) -
-                                  fminf(fmaxf(fmaf(-rhi.p1, T, rhi.pt0), 0.f), az);
-                else d = fminf(fmaxf(hh, 0.f), az) - fminf(fmaxf(hl, 0.f), az);
-                if (A > atiny && d > 0.f) sink.pair(pass, cstart + c, m, A * d * iD2);
+        const float zc = fmaf((float)k, az, G.z0) - V.sz;
+        const float iD2 = 1.0f / fmaf(C.tc, C.tc, fmaf(C.xc, C.xc, zc * zc));
+        const float gz = V.gv * zc;
+        for (int c = 0; c < ncol; ++c) {
+            const float4 fa = ws->fa[c];           // A_n, t_n, 1/t_n, hv
+            if (!(fa.x > 0.f)) continue;
+            const float hv = fa.w;
+            const float vn = fmaf(gz, fa.z, V.cv);
+            const int m_first = max((int)floorf(vn - hv + 0.5f), 0);
+            const int m_last = min((int)floorf(vn + hv + 0.5f), G.nv - 1);
+            if (m_last - m_first + 2 > KCT_ROWS) { atomicOr(err, 1); continue; }
+            const float w = fa.x * fa.y * V.inv_agv * iD2;
+            float e = -fmaf(gz, fa.z, V.cv - (float)m_first);   // m_first - v_n
+            const int n = cstart + c;
+            for (int m = m_first; m <= m_last; ++m, e += 1.0f) {
+                const float d = fminf(hv, e + 0.5f) - fmaxf(-hv, e - 0.5f);
+                if (d > 0.f) sink.pair(pass, n, m, w * d);
             }
-            rlo = rhi;
         }
         sink.end(pass, k);
     }
@@ -313,17 +334,27 @@ __device__ __forceinline__ void warp_column(const View& V, const Grid& G, int i,
         if (lane == 0) atomicOr(err, 1);
         return;
     }
-    __syncwarp();                  // the previous column's readers of ws are done
-    if (lane == 0) ws->C = C;
     for (int cstart = C.n_first; cstart <= C.n_last; cstart += KCT_CB) {
         const int ncol = min(KCT_CB, C.n_last - cstart + 1);
-        __syncwarp();
+        __syncwarp();              // the previous readers of ws are done
         if (lane < ncol) {
-            const Mom f = cut_moments_call(&V, &ws->C, cstart + lane, 3.0e38f);
-            if (VARIANT == 1) ws->fa[lane] = make_float4(f.m1, f.m1 > 0.f ? f.mt / f.m1 : 0.f, 0.f, 0.f);
-            else {
+            // H_n for n = cstart + lane: its vertices, moments and depth range
+            Line lo, hi;
+            column_lines(V, C, cstart + lane, lo, hi);
+            float* pt = ws->pt[lane];
+            float* px = ws->px[lane];
+            const int nv = clip_square(V, lo, hi, pt, px);
+            ws->nv[lane] = nv;
+            const Mom f = normalise(polygon_cut<true>(pt, px, nv, 3.0e38f), C.tc, C.xc);
+            float tlo = 3.0e38f, thi = -3.0e38f;
+            for (int q = 0; q < nv; ++q) { tlo = fminf(tlo, pt[q]); thi = fmaxf(thi, pt[q]); }
+            if (VARIANT == 1) {
+                const float tn = C.tc + (f.m1 > 0.f ? f.mt / f.m1 : 0.f);
+                const float itn = 1.0f / tn;
+                ws->fa[lane] = make_float4(f.m1, tn, itn, 0.5f * G.az * fabsf(V.gv) * itn);
+            } else {
                 ws->fa[lane] = make_float4(f.m1, f.mt, f.mtt, f.ml);
-                ws->fb[lane] = f.mlt;
+                ws->fb[lane] = make_float4(f.mlt, tlo, thi, 0.f);
             }
         }
         __syncwarp();
