@@ -144,6 +144,7 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
         const float zs = zc * V.sgv;
         const float D2 = fmaf(C.tc, C.tc, fmaf(C.xc, C.xc, zc * zc));
         if (act) sink.begin(pass, k);
+#pragma unroll 1
         for (int c = 0; c < ncol; ++c) {
             const float4 fa = ws->fa[c], fb = ws->fb[c];
             const float tlo = fb.y, thi = fb.z;
@@ -167,6 +168,7 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
             const float p1_0 = ((float)m_first - 0.5f - V.cv) * V.inv_agv;
             // classes of the boundaries: 0 / az for planes outside the voxel, crossing mask
             unsigned cross = 0u, zero = 0u, full = 0u;
+#pragma unroll 1
             for (int b = 0; b <= R; ++b) {
                 const float p0 = fmaf(0.5f, az, fmaf((float)b, dp0, off0)), p1 = fmaf((float)b, dp1, p1_0);
                 const float h0 = fmaf(p1, tlo, p0), h1 = fmaf(p1, thi, p0);
@@ -242,6 +244,7 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
                 // 3) pairs of the group's voxels with detector column n
                 if (lane >= lo_lane && lane < hi_lane && R > 0) {
                     const int n = cstart + c;
+#pragma unroll 1
                     for (int r = 0; r < R; ++r) {
                         const int m = m_first + r;
                         const unsigned bl = 1u << r, bh = 2u << r;
@@ -323,6 +326,31 @@ __device__ __forceinline__ void relaxed_voxels(const View& V, const Grid& G, con
     }
 }
 
+// H_n for detector column n: its vertices, moments and depth range into ws slot c.
+// Not inlined: it runs once per column and view.
+__device__ __noinline__ void build_column_cut(const View* Vp, const Column* Cp, float az, int n, int variant,
+                                              WarpSmem* ws, int c) {
+    const View& V = *Vp;
+    const Column& C = *Cp;
+    Line lo, hi;
+    column_lines(V, C, n, lo, hi);
+    float* pt = ws->pt[c];
+    float* px = ws->px[c];
+    const int nv = clip_square(V, lo, hi, pt, px);
+    ws->nv[c] = nv;
+    const Mom f = normalise(polygon_cut<true>(pt, px, nv, 3.0e38f), C.tc, C.xc);
+    float tlo = 3.0e38f, thi = -3.0e38f;
+    for (int q = 0; q < nv; ++q) { tlo = fminf(tlo, pt[q]); thi = fmaxf(thi, pt[q]); }
+    if (variant == 1) {
+        const float tn = C.tc + (f.m1 > 0.f ? f.mt / f.m1 : 0.f);
+        const float itn = 1.0f / tn;
+        ws->fa[c] = make_float4(f.m1, tn, itn, 0.5f * az * fabsf(V.gv) * itn);
+    } else {
+        ws->fa[c] = make_float4(f.m1, f.mt, f.mtt, f.ml);
+        ws->fb[c] = make_float4(f.mlt, tlo, thi, 0.f);
+    }
+}
+
 // All pairs of voxels kbase .. kbase + SEG - 1 of column (i, j) in view V (in shared memory).
 // Called by all 32 lanes of a warp with the same arguments.
 template <int VARIANT, class Sink>
@@ -337,26 +365,7 @@ __device__ __forceinline__ void warp_column(const View& V, const Grid& G, int i,
     for (int cstart = C.n_first; cstart <= C.n_last; cstart += KCT_CB) {
         const int ncol = min(KCT_CB, C.n_last - cstart + 1);
         __syncwarp();              // the previous readers of ws are done
-        if (lane < ncol) {
-            // H_n for n = cstart + lane: its vertices, moments and depth range
-            Line lo, hi;
-            column_lines(V, C, cstart + lane, lo, hi);
-            float* pt = ws->pt[lane];
-            float* px = ws->px[lane];
-            const int nv = clip_square(V, lo, hi, pt, px);
-            ws->nv[lane] = nv;
-            const Mom f = normalise(polygon_cut<true>(pt, px, nv, 3.0e38f), C.tc, C.xc);
-            float tlo = 3.0e38f, thi = -3.0e38f;
-            for (int q = 0; q < nv; ++q) { tlo = fminf(tlo, pt[q]); thi = fmaxf(thi, pt[q]); }
-            if (VARIANT == 1) {
-                const float tn = C.tc + (f.m1 > 0.f ? f.mt / f.m1 : 0.f);
-                const float itn = 1.0f / tn;
-                ws->fa[lane] = make_float4(f.m1, tn, itn, 0.5f * G.az * fabsf(V.gv) * itn);
-            } else {
-                ws->fa[lane] = make_float4(f.m1, f.mt, f.mtt, f.ml);
-                ws->fb[lane] = make_float4(f.mlt, tlo, thi, 0.f);
-            }
-        }
+        if (lane < ncol) build_column_cut(&V, &C, G.az, cstart + lane, VARIANT, ws, lane);
         __syncwarp();
         if (VARIANT == 1) relaxed_voxels(V, G, C, cstart, ncol, kbase, lane, ws, sink, err);
         else exact_voxels(V, G, C, cstart, ncol, kbase, lane, ws, sink, err);

@@ -47,10 +47,11 @@ _lib = None
 
 
 def load(path: str | None = None):
-    """Load libkct.so. Raises if it is missing: there is no fallback path."""
+    """Load libkct.so (or the library named by $KCT_LIB). Raises if it is missing: there is
+    no fallback path."""
     global _lib
     if _lib is None:
-        p = path or LIB_PATH
+        p = path or os.environ.get("KCT_LIB") or LIB_PATH
         if not os.path.exists(p):
             raise ImportError(f"libkct.so not built ({p}); run `python -m paper_2110_09841_b300.build`")
         lib = ctypes.CDLL(p)
