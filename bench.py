@@ -30,10 +30,28 @@ WORKLOAD = "cvp512"
 METRIC = "CVP project+backproject Gvoxel·views/s at 512³×496 views; CGLS time-to-1e-3 residual"
 UNIT = "Gvoxel·views/s"
 
-# FP32 operations per voxel-view of the dominant (near-exact) kernels, counted by ncu
-# (thread-level executed FADD + FMUL + 2 * FFMA) on the 512^3 x 496 geometry and divided by
-# the voxel-views of the launch. None until measured.
-FLOP_PER_VV = {"exact project": None, "exact backproject": None}
+# Per-kernel counts from one ncu capture of each projector kernel on the benchmark geometry
+# restricted to 8 of its views (python bench.py --profile-case cvp512 --views 8 ...; see
+# profiles/projector_kernels_cvp512_8views.md):
+#   flop_per_vv  FP32 operations (thread-level FADD + FMUL + 2 FFMA) per voxel-view,
+#   dram_8       DRAM bytes read + written by that 8-view launch.
+# A full 496-view launch processes 62x the voxel-views; the forward kernel re-reads the
+# volume once per chunk of 16 views and adds one projection per view, the adjoint reads one
+# projection tile per view and writes the volume once, so traffic is scaled as below.
+NCU = {
+    "exact project": {"flop_per_vv": 999.8, "dram_read_8": 5.808e8, "dram_write_8": 3.371e7},
+    "exact backproject": {"flop_per_vv": 1053.2, "dram_read_8": 6.111e7, "dram_write_8": 4.958e8},
+    "relaxed project": {"flop_per_vv": 165.5, "dram_read_8": 5.750e8, "dram_write_8": 3.268e7},
+    "relaxed backproject": {"flop_per_vv": 188.0, "dram_read_8": 4.954e7, "dram_write_8": 4.889e8},
+}
+
+
+def full_launch_traffic(name: str, nviews: int) -> float:
+    c = NCU[name]
+    if name.endswith("backproject"):      # per-view tile reads scale, the volume write does not
+        return c["dram_read_8"] * nviews / 8 + c["dram_write_8"]
+    chunks = (nviews + 15) // 16           # volume re-read per 16-view chunk, writes per view
+    return c["dram_read_8"] * chunks + c["dram_write_8"] * nviews / 8
 
 
 def parse():
@@ -326,11 +344,14 @@ def run_kct(args):
                        key=lambda q: per[q[0]][q[1]])
     dom_ms = per[dom_v][dom_k]
     name = f"{dom_v} {dom_k[:-3]}"
-    flop_vv = FLOP_PER_VV.get(name)
+    flop_vv = NCU[name]["flop_per_vv"] if args.workload == WORKLOAD else None
     achieved = (flop_vv * geom.voxel_views / (dom_ms / 1e3) / 1e12) if flop_vv else None
+    traffic = full_launch_traffic(name, geom.nviews) if args.workload == WORKLOAD else None
     roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": (achieved / peak_tflops) if achieved else None, "traffic": None,
-                "peak_basis": f"FP32 FMA: {sms} SMs x 128 lanes x 2 FLOP x {max_mhz:.0f} MHz (derived)"}
+                "frac": (achieved / peak_tflops) if achieved else None, "traffic": traffic,
+                "traffic_unit": "bytes per launch (ncu, 8-view capture scaled to the full launch)",
+                "launch_ms": dom_ms, "flop_per_voxel_view": flop_vv,
+                "peak_basis": f"FP32 FMA: {sms} SMs x 128 lanes x 2 FLOP x {max_mhz:.0f} MHz (derived, no measured FP32 peak)"}
 
     cb_val, cb_desc, cb_threads = cpu_baseline(geom, 10.0)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
