@@ -365,7 +365,7 @@ def run_kct(args):
            "variants": per, "roofline": roofline,
            "cpu_baseline": {"value": cb_val / 1e9, "unit": UNIT, "cores": cb_threads, "kind": "oracle",
                             "sample": cb_desc},
-           "e2e": e2e, "gpu_launches": 8 * args.steps, "clocks": clocks}
+           "e2e": e2e, "gpu_launches": 4 * args.steps, "clocks": clocks}
     print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist

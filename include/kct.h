@@ -95,8 +95,9 @@ typedef struct kct_plan kct_plan;
  *   nviews  number of views, >= 1.
  * Validates the arrangement above (KCT_ERR_GEOMETRY otherwise), converts each view to the
  * kernel's FP32 parameters (source, principal direction, detector scales) and uploads them.
- * The plan owns that device memory until kct_plan_destroy. Allocation failure returns
- * KCT_ERR_OOM. On error *out is set to NULL.
+ * The plan owns that device memory (a few hundred bytes per view) until kct_plan_destroy.
+ * Allocation failure returns KCT_ERR_OOM. On error *out is set to NULL. A plan may be used
+ * from several streams at once: calls share only read-only state and the error word.
  */
 kct_status kct_plan_create(kct_plan **out, const kct_volume_desc *vol, const kct_detector_desc *det,
                            const double *pmats, int32_t nviews, kct_variant variant,
@@ -126,6 +127,23 @@ kct_status kct_project(const kct_plan *plan, const float *d_vol, float *d_proj, 
  */
 kct_status kct_backproject(const kct_plan *plan, const float *d_proj, float *d_vol, int32_t accumulate,
                            void *stream);
+
+/*
+ * Batched forward projection: nbatch volumes, contiguous [nbatch][nz][ny][nx], through the
+ * plan's views into nbatch projection stacks [nbatch][nviews][nv][nu], in one launch.
+ * Same semantics as kct_project per batch member; ceil(nviews / 16) * nbatch must not
+ * exceed 65535 (KCT_ERR_UNSUPPORTED otherwise).
+ */
+kct_status kct_project_batch(const kct_plan *plan, const float *d_vol, int32_t nbatch, float *d_proj,
+                             int32_t accumulate, void *stream);
+
+/*
+ * Batched adjoint: nbatch projection stacks [nbatch][nviews][nv][nu] into nbatch volumes
+ * [nbatch][nz][ny][nx], in one launch; 1 <= nbatch <= 65535. Same semantics as
+ * kct_backproject per batch member.
+ */
+kct_status kct_backproject_batch(const kct_plan *plan, const float *d_proj, int32_t nbatch, float *d_vol,
+                                 int32_t accumulate, void *stream);
 
 /*
  * Pixel factors F(u, v) of every view of the plan (its scaling mode) into

@@ -410,11 +410,16 @@ __device__ __forceinline__ Tile brick_tile(const View& V, const Grid& G, int i0,
 // Sinks
 // ---------------------------------------------------------------------------------------
 
-struct FwdSink {      // tile[m][n] += mu * W  (unscaled sums of Eq. cvpsu)
+// Forward sink: tile[m][n] += mu * W (sums of Eq. cvpsu). Pairs that fall outside the
+// brick's tile go straight to the global output, multiplied by the pixel factor when the
+// kernel applies it (SCALING >= 0); SCALING < 0 leaves the sums unscaled.
+template <int SCALING>
+struct FwdSink {
+    const View* V;
     const float* mu_s;             // brick attenuation values, [SEG][BY][BX] in shared memory
     float* tile;
     Tile T;
-    float* __restrict__ Sg;        // global sums of the view (used where the tile does not reach)
+    float* __restrict__ Sg;        // global output of the view
     int nu, col, kbase;
     float mu;
     __device__ __forceinline__ void begin(int, int k) { mu = mu_s[(k - kbase) * NCOLS + col]; }
@@ -423,11 +428,15 @@ struct FwdSink {      // tile[m][n] += mu * W  (unscaled sums of Eq. cvpsu)
         if (mu == 0.f) return;
         const int du = n - T.u0, dv = m - T.v0;
         if (T.ok && (unsigned)du < (unsigned)T.w && (unsigned)dv < (unsigned)T.h) atomicAdd(&tile[dv * T.w + du], mu * W);
-        else atomicAdd(&Sg[(size_t)m * nu + n], mu * W);
+        else atomicAdd(&Sg[(size_t)m * nu + n], SCALING >= 0 ? mu * W * pixel_factor<(SCALING > 0)>(*V, n, m) : mu * W);
     }
 };
 
-struct BwdSink {      // acc += W * (F y)[m][n]
+// Adjoint sink: acc += W * F y. The staged tile already holds F y; pairs outside it read y
+// and apply F here.
+template <int SCALING>
+struct BwdSink {
+    const View* V;
     const float* tile;
     Tile T;
     const float* __restrict__ yg;
@@ -438,7 +447,8 @@ struct BwdSink {      // acc += W * (F y)[m][n]
     __device__ __forceinline__ void pair(int p, int n, int m, float W) {
         const int du = n - T.u0, dv = m - T.v0;
         const float y = (T.ok && (unsigned)du < (unsigned)T.w && (unsigned)dv < (unsigned)T.h)
-                            ? tile[dv * T.w + du] : __ldg(&yg[(size_t)m * nu + n]);
+                            ? tile[dv * T.w + du]
+                            : __ldg(&yg[(size_t)m * nu + n]) * pixel_factor<SCALING>(*V, n, m);
 #pragma unroll
         for (int q = 0; q < KPL; ++q)
             if (q == p) acc[q] = fmaf(W, y, acc[q]);
@@ -462,12 +472,16 @@ __device__ __forceinline__ void brick_origin(const Grid& G, int& i0, int& j0) {
 // Kernels
 // ---------------------------------------------------------------------------------------
 
-// grid: (bricks in x1 x2, segments along x3, view chunks); S receives the unscaled sums.
+// Forward projection. grid: (bricks in x1 x2, segments along x3, view chunks x batch).
+// Volume b of the batch starts at vol + b * vstride, its projections at out + b * pstride.
+// SCALING 0 / 1 multiplies by the cos / exact pixel factor while the tile is flushed;
+// SCALING < 0 leaves the unscaled sums of Eq. cvpsu. out must be zeroed (or hold the values
+// to add to) before the launch.
 // Dynamic shared memory: SEG * NCOLS + TILE_CAP floats.
-template <int VARIANT>
+template <int VARIANT, int SCALING>
 __global__ void __launch_bounds__(NTHREADS, 2) fwd_kernel(const View* __restrict__ views, Grid G,
-                                                          const float* __restrict__ vol, float* __restrict__ S,
-                                                          int* err) {
+                                                          const float* __restrict__ vol, float* __restrict__ out,
+                                                          long long vstride, long long pstride, int* err) {
     extern __shared__ float dyn[];
     __shared__ BlockSmem bs;
     float* mu_s = dyn;
@@ -476,13 +490,17 @@ __global__ void __launch_bounds__(NTHREADS, 2) fwd_kernel(const View* __restrict
     int i0, j0;
     brick_origin(G, i0, j0);
     const int kbase = blockIdx.y * SEG;
+    const int nchunk = (G.nviews + VIEW_CHUNK - 1) / VIEW_CHUNK;
+    const int chunk = blockIdx.z % nchunk, batch = blockIdx.z / nchunk;
+    vol += batch * vstride;
+    out += batch * pstride;
     for (int q = threadIdx.x; q < SEG * NCOLS; q += NTHREADS) {
         const int kk = q / NCOLS, c = q % NCOLS;
         const int i = i0 + c % BX, j = j0 + c / BX, k = kbase + kk;
         mu_s[q] = (i < G.nx && j < G.ny && k < G.nz) ? __ldg(&vol[((size_t)k * G.ny + j) * G.nx + i]) : 0.f;
     }
-    const int v_end = min((int)(blockIdx.z + 1) * VIEW_CHUNK, G.nviews);
-    for (int view = blockIdx.z * VIEW_CHUNK; view < v_end; ++view) {
+    const int v_end = min((chunk + 1) * VIEW_CHUNK, G.nviews);
+    for (int view = chunk * VIEW_CHUNK; view < v_end; ++view) {
         __syncthreads();
         if (threadIdx.x == 0) {
             bs.V = views[view];
@@ -493,28 +511,33 @@ __global__ void __launch_bounds__(NTHREADS, 2) fwd_kernel(const View* __restrict
         if (T.ok)
             for (int q = threadIdx.x; q < T.w * T.h; q += NTHREADS) tile[q] = 0.f;
         __syncthreads();
-        float* Sv = S + (size_t)view * G.nu * G.nv;
+        float* Sv = out + (size_t)view * G.nu * G.nv;
         for (int c = warp; c < NCOLS; c += NWARP) {
             const int i = i0 + c % BX, j = j0 + c / BX;
             if (i >= G.nx || j >= G.ny) continue;
-            FwdSink s{mu_s, tile, T, Sv, G.nu, c, kbase, 0.f};
+            FwdSink<SCALING> s{&bs.V, mu_s, tile, T, Sv, G.nu, c, kbase, 0.f};
             warp_column<VARIANT>(bs.V, G, i, j, kbase, lane, &bs.ws[warp], s, err);
         }
         __syncthreads();
         if (T.ok)
             for (int q = threadIdx.x; q < T.w * T.h; q += NTHREADS) {
                 const float v = tile[q];
-                if (v != 0.f) atomicAdd(&Sv[(size_t)(T.v0 + q / T.w) * G.nu + T.u0 + q % T.w], v);
+                if (v != 0.f) {
+                    const int n = T.u0 + q % T.w, m = T.v0 + q / T.w;
+                    atomicAdd(&Sv[(size_t)m * G.nu + n], SCALING >= 0 ? v * pixel_factor<(SCALING > 0)>(bs.V, n, m) : v);
+                }
             }
     }
 }
 
-// grid: (bricks in x1 x2, segments along x3); every block loops over all views.
+// Adjoint. grid: (bricks in x1 x2, segments along x3, batch); every block loops over all
+// views, staging F y of the brick's footprint in shared memory per view.
 // Dynamic shared memory: SEG * NCOLS + TILE_CAP floats.
-template <int VARIANT>
+template <int VARIANT, int SCALING>
 __global__ void __launch_bounds__(NTHREADS, 2) bwd_kernel(const View* __restrict__ views, Grid G,
-                                                          const float* __restrict__ yF, float* __restrict__ vol,
-                                                          int accumulate, int* err) {
+                                                          const float* __restrict__ y, float* __restrict__ vol,
+                                                          long long vstride, long long pstride, int accumulate,
+                                                          int* err) {
     extern __shared__ float dyn[];
     __shared__ BlockSmem bs;
     float* acc_s = dyn;                 // [NCOLS][SEG]
@@ -523,6 +546,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) bwd_kernel(const View* __restrict
     int i0, j0;
     brick_origin(G, i0, j0);
     const int kbase = blockIdx.y * SEG;
+    vol += blockIdx.z * vstride;
+    y += blockIdx.z * pstride;
     for (int q = threadIdx.x; q < SEG * NCOLS; q += NTHREADS) acc_s[q] = 0.f;
     for (int view = 0; view < G.nviews; ++view) {
         __syncthreads();
@@ -532,15 +557,17 @@ __global__ void __launch_bounds__(NTHREADS, 2) bwd_kernel(const View* __restrict
         }
         __syncthreads();
         const Tile T = bs.T;
-        const float* yv = yF + (size_t)view * G.nu * G.nv;
+        const float* yv = y + (size_t)view * G.nu * G.nv;
         if (T.ok)
-            for (int q = threadIdx.x; q < T.w * T.h; q += NTHREADS)
-                tile[q] = __ldg(&yv[(size_t)(T.v0 + q / T.w) * G.nu + T.u0 + q % T.w]);
+            for (int q = threadIdx.x; q < T.w * T.h; q += NTHREADS) {
+                const int n = T.u0 + q % T.w, m = T.v0 + q / T.w;
+                tile[q] = __ldg(&yv[(size_t)m * G.nu + n]) * pixel_factor<SCALING>(bs.V, n, m);
+            }
         __syncthreads();
         for (int c = warp; c < NCOLS; c += NWARP) {
             const int i = i0 + c % BX, j = j0 + c / BX;
             if (i >= G.nx || j >= G.ny) continue;
-            BwdSink s{tile, T, yv, G.nu, {}};
+            BwdSink<SCALING> s{&bs.V, tile, T, yv, G.nu, {}};
 #pragma unroll
             for (int p = 0; p < KPL; ++p) s.acc[p] = 0.f;
             warp_column<VARIANT>(bs.V, G, i, j, kbase, lane, &bs.ws[warp], s, err);

@@ -29,7 +29,6 @@ struct kct_plan {
     View* d_views;
     int* d_err;
     unsigned long long* d_count;
-    float* d_work;      // projection-sized workspace: unscaled sums / pixel-scaled input
 };
 
 namespace {
@@ -171,41 +170,47 @@ unsigned segments(const Grid& G) { return (unsigned)((G.nz + kct::SEG - 1) / kct
 constexpr size_t kBrickDynSmem = sizeof(float) * (kct::SEG * kct::NCOLS + kct::TILE_CAP);
 
 // opt in to more than 48 KB of shared memory per block (once per process)
+template <class K>
+cudaError_t set_dyn(K kernel, cudaError_t e) {
+    return e == cudaSuccess ? cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBrickDynSmem) : e;
+}
+
 cudaError_t brick_kernel_attributes() {
     static cudaError_t done = [] {
         cudaError_t e = cudaSuccess;
-        const int dyn = (int)kBrickDynSmem;
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(kct::fwd_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(kct::fwd_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(kct::bwd_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(kct::bwd_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        e = set_dyn(kct::fwd_kernel<0, 0>, e);
+        e = set_dyn(kct::fwd_kernel<0, 1>, e);
+        e = set_dyn(kct::fwd_kernel<1, 0>, e);
+        e = set_dyn(kct::fwd_kernel<1, 1>, e);
+        e = set_dyn(kct::fwd_kernel<0, -1>, e);
+        e = set_dyn(kct::fwd_kernel<1, -1>, e);
+        e = set_dyn(kct::bwd_kernel<0, 0>, e);
+        e = set_dyn(kct::bwd_kernel<0, 1>, e);
+        e = set_dyn(kct::bwd_kernel<1, 0>, e);
+        e = set_dyn(kct::bwd_kernel<1, 1>, e);
         return e;
     }();
     return done;
 }
 
-template <int VARIANT>
-void launch_fwd(const kct_plan* p, const float* vol, float* S, cudaStream_t st) {
+unsigned view_chunks(const Grid& G) { return (unsigned)((G.nviews + kct::VIEW_CHUNK - 1) / kct::VIEW_CHUNK); }
+
+template <int VARIANT, int SCALING>
+void launch_fwd(const kct_plan* p, const float* vol, float* out, int nbatch, cudaStream_t st) {
     const Grid& G = p->grid;
-    dim3 grid(bricks(G), segments(G), (unsigned)((G.nviews + kct::VIEW_CHUNK - 1) / kct::VIEW_CHUNK));
-    kct::fwd_kernel<VARIANT><<<grid, kct::NTHREADS, kBrickDynSmem, st>>>(p->d_views, G, vol, S, p->d_err);
+    dim3 grid(bricks(G), segments(G), view_chunks(G) * (unsigned)nbatch);
+    const long long vs = (long long)G.nx * G.ny * G.nz, ps = (long long)G.nu * G.nv * G.nviews;
+    kct::fwd_kernel<VARIANT, SCALING><<<grid, kct::NTHREADS, kBrickDynSmem, st>>>(p->d_views, G, vol, out, vs, ps,
+                                                                                   p->d_err);
 }
 
-template <int VARIANT>
-void launch_bwd(const kct_plan* p, const float* yF, float* vol, int accumulate, cudaStream_t st) {
+template <int VARIANT, int SCALING>
+void launch_bwd(const kct_plan* p, const float* y, float* vol, int nbatch, int accumulate, cudaStream_t st) {
     const Grid& G = p->grid;
-    dim3 grid(bricks(G), segments(G));
-    kct::bwd_kernel<VARIANT><<<grid, kct::NTHREADS, kBrickDynSmem, st>>>(p->d_views, G, yF, vol, accumulate, p->d_err);
-}
-
-void launch_scale(const kct_plan* p, const float* in, float* out, int accumulate, cudaStream_t st) {
-    const Grid& G = p->grid;
-    long n = (long)G.nu * G.nv;
-    dim3 grid((unsigned)((n + 255) / 256), G.nviews);
-    if (p->scaling == KCT_SCALE_EXACT)
-        kct::scale_kernel<1><<<grid, 256, 0, st>>>(p->d_views, G, in, out, accumulate);
-    else
-        kct::scale_kernel<0><<<grid, 256, 0, st>>>(p->d_views, G, in, out, accumulate);
+    dim3 grid(bricks(G), segments(G), (unsigned)nbatch);
+    const long long vs = (long long)G.nx * G.ny * G.nz, ps = (long long)G.nu * G.nv * G.nviews;
+    kct::bwd_kernel<VARIANT, SCALING><<<grid, kct::NTHREADS, kBrickDynSmem, st>>>(p->d_views, G, y, vol, vs, ps,
+                                                                                   accumulate, p->d_err);
 }
 
 template <int VARIANT>
@@ -282,7 +287,6 @@ kct_status kct_plan_create(kct_plan** out, const kct_volume_desc* vol, const kct
     p->d_views = nullptr;
     p->d_err = nullptr;
     p->d_count = nullptr;
-    p->d_work = nullptr;
     p->h_views.resize(nviews);
     for (int q = 0; q < nviews; ++q) {
         std::string why = setup_view(pmats + 12 * q, *vol, p->h_views[q]);
@@ -310,19 +314,17 @@ kct_status kct_plan_create(kct_plan** out, const kct_volume_desc* vol, const kct
     if (e != cudaSuccess) { delete p; return fail(KCT_ERR_OOM, std::string("cudaMalloc views: ") + cudaGetErrorString(e)); }
     e = cudaMalloc(&p->d_err, sizeof(int) * 4);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_count, sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_work, sizeof(float) * (size_t)npix);
     if (e != cudaSuccess) {
         cudaFree(p->d_views);
         cudaFree(p->d_err);
         cudaFree(p->d_count);
-        cudaFree(p->d_work);
         delete p;
         return fail(KCT_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
     }
     e = cudaMemcpy(p->d_views, p->h_views.data(), sizeof(View) * nviews, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int) * 4);
     if (e != cudaSuccess) {
-        cudaFree(p->d_views); cudaFree(p->d_err); cudaFree(p->d_count); cudaFree(p->d_work);
+        cudaFree(p->d_views); cudaFree(p->d_err); cudaFree(p->d_count);
         delete p;
         return cuda_fail(e, "uploading view parameters");
     }
@@ -338,46 +340,76 @@ kct_status kct_plan_destroy(kct_plan* p) {
     cudaFree(p->d_views);
     cudaFree(p->d_err);
     cudaFree(p->d_count);
-    cudaFree(p->d_work);
     if (cur >= 0 && cur != p->device) cudaSetDevice(cur);
     delete p;
     return KCT_OK;
 }
 
-kct_status kct_project(const kct_plan* p, const float* d_vol, float* d_proj, int32_t accumulate, void* stream) {
+static kct_status project_impl(const kct_plan* p, const float* d_vol, float* d_proj, int32_t nbatch,
+                               int32_t accumulate, void* stream) {
     kct_status s = check_plan(p);
     if (s != KCT_OK) return s;
     if (!d_vol || !d_proj) return fail(KCT_ERR_INVALID_ARG, "null data pointer");
+    if (nbatch <= 0) return fail(KCT_ERR_INVALID_ARG, "nbatch must be positive");
+    const Grid& G = p->grid;
+    if ((long long)view_chunks(G) * nbatch > 65535) return fail(KCT_ERR_UNSUPPORTED, "batch too large for one launch");
     if ((s = set_device(p)) != KCT_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
-    const Grid& G = p->grid;
-    size_t pbytes = sizeof(float) * (size_t)G.nu * G.nv * G.nviews;
-    cudaError_t e = cudaMemsetAsync(p->d_work, 0, pbytes, st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    if (p->variant == KCT_CVP_RELAXED) launch_fwd<1>(p, d_vol, p->d_work, st);
-    else launch_fwd<0>(p, d_vol, p->d_work, st);
+    size_t pbytes = sizeof(float) * (size_t)G.nu * G.nv * G.nviews * nbatch;
+    cudaError_t e;
+    if (!accumulate) {
+        e = cudaMemsetAsync(d_proj, 0, pbytes, st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    }
+    const int key = (p->variant == KCT_CVP_RELAXED ? 2 : 0) + (p->scaling == KCT_SCALE_EXACT ? 1 : 0);
+    switch (key) {
+        case 0: launch_fwd<0, 0>(p, d_vol, d_proj, nbatch, st); break;
+        case 1: launch_fwd<0, 1>(p, d_vol, d_proj, nbatch, st); break;
+        case 2: launch_fwd<1, 0>(p, d_vol, d_proj, nbatch, st); break;
+        default: launch_fwd<1, 1>(p, d_vol, d_proj, nbatch, st); break;
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "forward projection launch");
-    launch_scale(p, p->d_work, d_proj, accumulate ? 1 : 0, st);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "pixel factor launch");
     return KCT_OK;
 }
 
-kct_status kct_backproject(const kct_plan* p, const float* d_proj, float* d_vol, int32_t accumulate, void* stream) {
+static kct_status backproject_impl(const kct_plan* p, const float* d_proj, float* d_vol, int32_t nbatch,
+                                   int32_t accumulate, void* stream) {
     kct_status s = check_plan(p);
     if (s != KCT_OK) return s;
     if (!d_vol || !d_proj) return fail(KCT_ERR_INVALID_ARG, "null data pointer");
+    if (nbatch <= 0 || nbatch > 65535) return fail(KCT_ERR_INVALID_ARG, "nbatch must be in [1, 65535]");
     if ((s = set_device(p)) != KCT_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
-    launch_scale(p, d_proj, p->d_work, 0, st);
+    const int key = (p->variant == KCT_CVP_RELAXED ? 2 : 0) + (p->scaling == KCT_SCALE_EXACT ? 1 : 0);
+    const int acc = accumulate ? 1 : 0;
+    switch (key) {
+        case 0: launch_bwd<0, 0>(p, d_proj, d_vol, nbatch, acc, st); break;
+        case 1: launch_bwd<0, 1>(p, d_proj, d_vol, nbatch, acc, st); break;
+        case 2: launch_bwd<1, 0>(p, d_proj, d_vol, nbatch, acc, st); break;
+        default: launch_bwd<1, 1>(p, d_proj, d_vol, nbatch, acc, st); break;
+    }
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "pixel factor launch");
-    if (p->variant == KCT_CVP_RELAXED) launch_bwd<1>(p, p->d_work, d_vol, accumulate ? 1 : 0, st);
-    else launch_bwd<0>(p, p->d_work, d_vol, accumulate ? 1 : 0, st);
-    e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "backprojection launch");
     return KCT_OK;
+}
+
+kct_status kct_project(const kct_plan* p, const float* d_vol, float* d_proj, int32_t accumulate, void* stream) {
+    return project_impl(p, d_vol, d_proj, 1, accumulate, stream);
+}
+
+kct_status kct_backproject(const kct_plan* p, const float* d_proj, float* d_vol, int32_t accumulate, void* stream) {
+    return backproject_impl(p, d_proj, d_vol, 1, accumulate, stream);
+}
+
+kct_status kct_project_batch(const kct_plan* p, const float* d_vol, int32_t nbatch, float* d_proj,
+                             int32_t accumulate, void* stream) {
+    return project_impl(p, d_vol, d_proj, nbatch, accumulate, stream);
+}
+
+kct_status kct_backproject_batch(const kct_plan* p, const float* d_proj, int32_t nbatch, float* d_vol,
+                                 int32_t accumulate, void* stream) {
+    return backproject_impl(p, d_proj, d_vol, nbatch, accumulate, stream);
 }
 
 kct_status kct_pixel_factors(const kct_plan* p, float* d_out, void* stream) {
@@ -538,9 +570,9 @@ extern "C" kct_status kct_project_static(const kct_volume_desc* vol, const kct_d
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     dim3 grid(bricks(G), segments(G), (unsigned)((G.nviews + kct::VIEW_CHUNK - 1) / kct::VIEW_CHUNK));
     if (variant == KCT_CVP_RELAXED)
-        kct::fwd_kernel<1><<<grid, kct::NTHREADS, kBrickDynSmem, st>>>(d_views, G, d_vol, S, d_err);
+        kct::fwd_kernel<1, -1><<<grid, kct::NTHREADS, kBrickDynSmem, st>>>(d_views, G, d_vol, S, 0, 0, d_err);
     else
-        kct::fwd_kernel<0><<<grid, kct::NTHREADS, kBrickDynSmem, st>>>(d_views, G, d_vol, S, d_err);
+        kct::fwd_kernel<0, -1><<<grid, kct::NTHREADS, kBrickDynSmem, st>>>(d_views, G, d_vol, S, 0, 0, d_err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "forward projection launch");
     dim3 sgrid((unsigned)(((long)G.nu * G.nv + 255) / 256), G.nviews);

@@ -24,7 +24,8 @@ STATUS = {0: "KCT_OK", 1: "KCT_ERR_INVALID_ARG", 2: "KCT_ERR_GEOMETRY", 3: "KCT_
 
 EXPORTED = ["kct_plan_create", "kct_plan_destroy", "kct_project", "kct_backproject",
             "kct_pixel_factors", "kct_count_pairs", "kct_last_device_error", "kct_status_string",
-            "kct_last_error_message", "kct_version", "kct_project_static"]
+            "kct_last_error_message", "kct_version", "kct_project_static", "kct_project_batch",
+            "kct_backproject_batch"]
 
 
 class KctError(RuntimeError):
@@ -65,6 +66,10 @@ def load(path: str | None = None):
         lib.kct_project.restype = I
         lib.kct_backproject.argtypes = [V, V, V, I32, V]
         lib.kct_backproject.restype = I
+        lib.kct_project_batch.argtypes = [V, V, I32, V, I32, V]
+        lib.kct_project_batch.restype = I
+        lib.kct_backproject_batch.argtypes = [V, V, I32, V, I32, V]
+        lib.kct_backproject_batch.restype = I
         lib.kct_pixel_factors.argtypes = [V, V, V]
         lib.kct_pixel_factors.restype = I
         lib.kct_count_pairs.argtypes = [V, ctypes.POINTER(ctypes.c_uint64), V]
@@ -169,6 +174,36 @@ class Projector:
             out = torch.empty(g.vol_shape, dtype=torch.float32, device=y.device)
         _check(self.lib.kct_backproject(self._h, yp, _dev_ptr(out, g.vol_shape, "out"), int(bool(accumulate)),
                                         _stream_handle(stream)))
+        return out
+
+    def project_batch(self, x, out=None, accumulate=False, stream=None):
+        """x: [B, nz, ny, nx] -> [B, nviews, nv, nu], one launch."""
+        import torch
+
+        g = self.geom
+        if x.dim() != 4:
+            raise ValueError("x must be [B, nz, ny, nx]")
+        B = int(x.shape[0])
+        xp = _dev_ptr(x, (B,) + g.vol_shape, "x")
+        if out is None:
+            out = torch.empty((B,) + g.proj_shape, dtype=torch.float32, device=x.device)
+        _check(self.lib.kct_project_batch(self._h, xp, B, _dev_ptr(out, (B,) + g.proj_shape, "out"),
+                                          int(bool(accumulate)), _stream_handle(stream)))
+        return out
+
+    def backproject_batch(self, y, out=None, accumulate=False, stream=None):
+        """y: [B, nviews, nv, nu] -> [B, nz, ny, nx], one launch."""
+        import torch
+
+        g = self.geom
+        if y.dim() != 4:
+            raise ValueError("y must be [B, nviews, nv, nu]")
+        B = int(y.shape[0])
+        yp = _dev_ptr(y, (B,) + g.proj_shape, "y")
+        if out is None:
+            out = torch.empty((B,) + g.vol_shape, dtype=torch.float32, device=y.device)
+        _check(self.lib.kct_backproject_batch(self._h, yp, B, _dev_ptr(out, (B,) + g.vol_shape, "out"),
+                                              int(bool(accumulate)), _stream_handle(stream)))
         return out
 
     def pixel_factors(self, stream=None):

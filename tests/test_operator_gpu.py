@@ -1,0 +1,115 @@
+"""The projector as a differentiable, batched operator on the GPU: autograd gradients against
+central finite differences and against the FP64 oracle's adjoint, batched launches against
+single ones, and replay of a captured CUDA graph."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2110_09841_b300 import autograd, inputs
+from paper_2110_09841_b300.kct import Projector
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+def sub16():
+    return inputs.make_geometry((16, 16, 16), (1.0, 1.0, 1.0), (40, 32), (0.8, 0.8), 9, 750.0, 1200.0, 360.0)
+
+
+@pytest.mark.parametrize("vname", ["exact", "relaxed"])
+def test_gradient_matches_central_differences(vname):
+    """d/dx 0.5 |A x - y|^2 = A^T (A x - y); for a quadratic loss the central difference with
+    h = 1e-3 differs from the directional derivative only by rounding."""
+    g = sub16()
+    A = Projector(g, vname, "cos")
+    x = inputs.uniform_volume(g.vol_shape, 1, device="cuda").requires_grad_(True)
+    y = inputs.uniform_projections(g.proj_shape, 2, device="cuda")
+    d = inputs.uniform_volume(g.vol_shape, 3, device="cuda") - 0.5
+
+    def loss(v):
+        r = (autograd.project(v, A) - y).double()
+        return 0.5 * (r * r).sum()
+
+    L = loss(x)
+    L.backward()
+    gd = float((x.grad.double() * d.double()).sum())
+    h = 1e-3
+    with torch.no_grad():
+        fd = (float(loss(x + h * d)) - float(loss(x - h * d))) / (2 * h)
+    assert abs(gd - fd) <= 2e-4 * abs(fd)
+
+
+def test_gradient_matches_oracle_adjoint():
+    g = sub16()
+    A = Projector(g, "exact", "cos")
+    x = inputs.uniform_volume(g.vol_shape, 4, device="cuda").requires_grad_(True)
+    y = inputs.uniform_projections(g.proj_shape, 5, device="cuda")
+    r = autograd.project(x, A) - y
+    (0.5 * (r * r).sum()).backward()
+    ref = oracle.backproject(g, r.detach().cpu().double().numpy(), 0, 0)
+    got = x.grad.cpu().double().numpy()
+    mx = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= TOL * mx
+    big = np.abs(ref) >= 1e-3 * mx
+    assert (np.abs(got - ref)[big] / np.abs(ref[big])).max() <= TOL
+
+
+def test_backproject_function_gradient_is_projection():
+    g = sub16()
+    A = Projector(g, "relaxed", "cos")
+    y = inputs.uniform_projections(g.proj_shape, 6, device="cuda").requires_grad_(True)
+    w = inputs.uniform_volume(g.vol_shape, 7, device="cuda")
+    (autograd.backproject(y, A) * w).sum().backward()
+    ref = A.project(w)
+    torch.testing.assert_close(y.grad, ref, rtol=1e-5, atol=1e-6 * float(ref.abs().max()))
+
+
+@pytest.mark.parametrize("vname", ["exact", "relaxed"])
+def test_batched_launch_equals_single_launches(vname):
+    """A batch of perfusion-like frames through shared views in one launch."""
+    g = inputs.make_geometry((24, 24, 20), (1.0, 1.0, 1.0), (48, 40), (0.8, 0.8), 20, 750.0, 1200.0, 360.0)
+    frames = inputs.perfusion_frames(g, 31, frames=4, device="cuda")
+    A = Projector(g, vname, "cos")
+    b = A.project_batch(frames)
+    for f in range(4):
+        ref = A.project(frames[f].contiguous())
+        torch.testing.assert_close(b[f], ref, rtol=1e-5, atol=1e-6 * float(ref.abs().max()))
+    y = inputs.uniform_projections((4,) + g.proj_shape, 8, device="cuda")
+    xb = A.backproject_batch(y)
+    for f in range(4):
+        torch.testing.assert_close(xb[f], A.backproject(y[f].contiguous()), rtol=0, atol=0)
+    # autograd through the batched path
+    fr = frames.clone().requires_grad_(True)
+    (autograd.project(fr, A) * y).sum().backward()
+    torch.testing.assert_close(fr.grad, xb, rtol=0, atol=0)
+
+
+def test_captured_graph_replays():
+    """Projection and adjoint enqueue work only (no allocation, no synchronisation), so they
+    can be captured in a CUDA graph and replayed on new inputs."""
+    g = inputs.workload_geometry("cvp32")
+    A = Projector(g, "exact", "cos")
+    x = torch.zeros(g.vol_shape, device="cuda")
+    y = torch.zeros(g.proj_shape, device="cuda")
+    b = torch.empty(g.proj_shape, device="cuda")
+    xb = torch.empty(g.vol_shape, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        A.project(x, out=b)
+        A.backproject(y, out=xb)
+    torch.cuda.current_stream().wait_stream(s)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        A.project(x, out=b)
+        A.backproject(y, out=xb)
+    for seed in (1, 2):
+        x.copy_(inputs.workload_phantom("cvp32").cuda() * seed)
+        y.copy_(inputs.uniform_projections(g.proj_shape, seed, device="cuda"))
+        graph.replay()
+        torch.cuda.synchronize()
+        rb, rx = A.project(x), A.backproject(y)
+        torch.testing.assert_close(b, rb, rtol=1e-5, atol=1e-6 * float(rb.abs().max()))
+        torch.testing.assert_close(xb, rx, rtol=0, atol=0)
