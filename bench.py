@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--scaling", default="cos", choices=["cos", "exact"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cgls", action="store_true")
+    ap.add_argument("--cgls-max-iter", type=int, default=200)
     ap.add_argument("--profile-case", default=None, metavar="WORKLOAD",
                     help="run one projector call on a sub-sampled workload (for ncu captures) and exit")
     ap.add_argument("--variant", default="exact", choices=["exact", "relaxed"])
@@ -98,6 +100,26 @@ def run_profile_case(args):
     ms = e0.elapsed_time(e1)
     print(json.dumps({"case": args.profile_case, "views": g.nviews, "variant": args.variant,
                       "direction": args.direction, "ms": ms, "gvv_s": g.voxel_views / (ms / 1e3) / 1e9}))
+
+
+E2E_STEPS = 1      # steps of the end-to-end measurement (after one untimed end-to-end step)
+
+
+def max_over_ranks(ms: float, device) -> float:
+    """The slowest rank's time: every rank returns the maximum over the process group."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_gvv_s(units_per_step: float, steps: int, ms: float, world: int) -> float:
+    """Whole-job throughput: every replica processes units_per_step voxel-views per step."""
+    return world * units_per_step * steps / (ms / 1e3) / 1e9
 
 
 def dist_env():
@@ -191,6 +213,43 @@ WORKLOAD_DESC = ("cvp512: 512^3 voxels @ 0.25 mm, 496 views / 360 deg, SID 400 /
                  "1232x960 detector @ 0.154 mm, seeded 40-ellipsoid phantom")
 
 
+CGLS_DESC = ("cgls128: 128^3 voxels @ 0.5 mm, 180 views / 360 deg, SID 750 / SDD 1200 mm, 256x192 detector "
+             "@ 0.8 mm, seeded 20-ellipsoid phantom, Poisson noise at 1e5 photons per pixel, CGLS from 0")
+
+
+def run_cgls(dev, scaling: str, max_iter: int, tol: float = 1e-3):
+    """Time to the normal-equation residual |A^T(b - A x)| / |A^T b| <= tol with kct_cgls, for
+    both variants, on noisy projections of a seeded phantom made with the same variant.
+    The timed region is the whole kct_cgls call (start, steps, per-step residual reads)."""
+    import torch
+
+    from paper_2110_09841_b300 import inputs
+    from paper_2110_09841_b300.kct import Projector
+
+    g = inputs.workload_geometry("cgls128")
+    truth = inputs.workload_phantom("cgls128", device=dev)
+    out = {"workload": CGLS_DESC, "tol": tol, "max_iter": max_iter}
+    for v in ("exact", "relaxed"):
+        A = Projector(g, v, scaling)
+        b = inputs.poisson_log_data(A.project(truth), 1e5, 77)
+        ws = A.cgls_workspace()
+        x = torch.empty(g.vol_shape, dtype=torch.float32, device=dev)
+        A.cgls(b, max_iter=2, tol=0.0, out=x, workspace=ws)          # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        x, info = A.cgls(b, max_iter=max_iter, tol=tol, out=x, workspace=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        k = info["iterations"]
+        out[v] = {"iterations": k, "converged": info["converged"], "time_s": ms / 1e3,
+                  "ms_per_iteration": ms / max(k, 1), "normal_residual": float(info["normal"][-1]),
+                  "data_residual": float(info["data"][-1]),
+                  "rel_error_vs_phantom": float((x - truth).norm() / truth.norm())}
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -282,14 +341,9 @@ def run_kct(args):
     per = {v: {"project_ms": statistics.median(e[v][0].elapsed_time(e[v][1]) for e in events),
                "backproject_ms": statistics.median(e[v][1].elapsed_time(e[v][2]) for e in events)}
            for v in variants}
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dev)
     units_per_step = 2 * geom.voxel_views          # one P+BP per variant
-    value = world * units_per_step * args.steps / (total_ms / 1e3) / 1e9
+    value = aggregate_gvv_s(units_per_step, args.steps, total_ms, world)
     for v in variants:
         p = per[v]
         p["p_bp_gvv_s"] = geom.voxel_views / ((p["project_ms"] + p["backproject_ms"]) / 1e3) / 1e9
@@ -319,14 +373,16 @@ def run_kct(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(E2E_STEPS):
             e2e_step()
         e1.record(stream)
         barrier()
-        ems = e0.elapsed_time(e1)
-        e2e = {"value": world * units_per_step * args.steps / (ems / 1e3) / 1e9, "unit": UNIT,
+        ems = max_over_ranks(e0.elapsed_time(e1), dev)
+        e2e = {"value": aggregate_gvv_s(units_per_step, E2E_STEPS, ems, world), "unit": UNIT, "steps": E2E_STEPS,
                "h2d_bytes_per_step": (x.numel() + y.numel()) * 4,
                "d2h_bytes_per_step": len(variants) * (x.numel() + y.numel()) * 4}
+
+    cgls = None if args.no_cgls else run_cgls(dev, args.scaling, args.cgls_max_iter)
 
     if rank != 0:
         if world > 1:
@@ -365,7 +421,7 @@ def run_kct(args):
            "variants": per, "roofline": roofline,
            "cpu_baseline": {"value": cb_val / 1e9, "unit": UNIT, "cores": cb_threads, "kind": "oracle",
                             "sample": cb_desc},
-           "e2e": e2e, "gpu_launches": 4 * args.steps, "clocks": clocks}
+           "e2e": e2e, "gpu_launches": 4 * args.steps, "clocks": clocks, "cgls": cgls}
     print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -146,6 +146,28 @@ kct_status kct_backproject_batch(const kct_plan *plan, const float *d_proj, int3
                                  int32_t accumulate, void *stream);
 
 /*
+ * Forward-kernel tuning. Each forward block takes one brick of voxels (8 x 8 columns x 64
+ * voxels) through `chunk` consecutive views; more views per block re-read the brick from
+ * HBM less often, fewer give more blocks to small problems. Default 16.
+ *
+ * kct_plan_autotune times one forward projection of d_vol with each candidate chunk
+ * (1, 2, 4, 8, 16, 32, 64; a warm-up launch, then a timed one, CUDA events on `stream`) over
+ * the plan's first min(nviews, 64) views, and keeps the fastest in the plan.
+ *   d_vol   device float32 [nz][ny][nx], read only (the volume the timing uses).
+ *   d_proj  device float32 [nviews][nv][nu]; its first min(nviews, 64) views are
+ *           overwritten with scratch.
+ *   chunk   optional: receives the chosen chunk.   ms: optional: its forward time (ms).
+ * Synchronises `stream`; not for stream capture. Tune before capturing graphs that use
+ * the plan: a captured launch keeps the chunk it was captured with.
+ * kct_plan_set_view_chunk sets the chunk directly (1..64, KCT_ERR_INVALID_ARG otherwise);
+ * kct_plan_get_view_chunk reads it. Work already enqueued keeps its chunk.
+ */
+kct_status kct_plan_autotune(kct_plan *plan, const float *d_vol, float *d_proj, int32_t *chunk, float *ms,
+                             void *stream);
+kct_status kct_plan_set_view_chunk(kct_plan *plan, int32_t chunk);
+kct_status kct_plan_get_view_chunk(const kct_plan *plan, int32_t *chunk);
+
+/*
  * Pixel factors F(u, v) of every view of the plan (its scaling mode) into
  * d_out, device float32 [nviews][nv][nu]. Enqueued on `stream`.
  */
@@ -182,6 +204,44 @@ kct_status kct_last_device_error(const kct_plan *plan, int32_t *code, void *stre
 kct_status kct_project_static(const kct_volume_desc *vol, const kct_detector_desc *det, const double *pmats,
                               int32_t nviews, kct_variant variant, kct_scaling scaling, const float *d_vol,
                               float *d_proj, int32_t accumulate, void *stream);
+
+/*
+ * CGLS reconstruction with the plan's operator: conjugate gradients on the normal equations
+ * A^T A x = A^T b, applying A and A^T once per step (the reconstruction that drives the
+ * projector timings of Sec. IV-A; Krylov methods of Sec. V "Software"; textbook CGLS,
+ * Bjorck 1996, Sec. 7.4). Per step: one kct_project, one kct_backproject and four vector
+ * kernels (squared norms, x += alpha p with r -= alpha q, p = s + beta p); alpha and beta
+ * stay on the device.
+ *
+ * Stopping rule: the normal-equation residual |A^T (b - A x_k)| / |A^T b| <= tol, checked
+ * after every step (and once before the first, so a start that already meets it takes no
+ * step), or max_iter steps.
+ *
+ *   d_b        device float32 [nviews][nv][nu], read only.
+ *   d_x        device float32 [nz][ny][nx]: on entry the start x0 if warm_start != 0
+ *              (ignored otherwise: the start is 0); on return the solution.
+ *   max_iter   >= 0.   tol >= 0 (0 runs max_iter steps).
+ *   d_work     device scratch of at least kct_cgls_workspace_bytes(plan) bytes, 256-byte
+ *              aligned; owned by the caller, contents on entry ignored.
+ *   h_normal, h_data   optional host arrays of max_iter + 1 doubles (NULL to skip): entry k
+ *              gets the normal residual and |b - A x_k| / |b| after k steps.
+ *   report     optional: steps taken, whether tol was met, and the final residuals.
+ * d_b and d_x must be 16-byte aligned and must not overlap d_work.
+ * Synchronous: it reads the residuals from the device after every step (one 16-byte copy and
+ * a stream synchronisation) and returns when the solve is done. Not for stream capture.
+ */
+typedef struct kct_cgls_report {
+    int32_t iterations;        /* steps taken */
+    int32_t converged;         /* 1 if the normal residual reached tol */
+    double normal_residual;    /* |A^T (b - A x)| / |A^T b| at return */
+    double data_residual;      /* |b - A x| / |b| at return */
+} kct_cgls_report;
+
+size_t kct_cgls_workspace_bytes(const kct_plan *plan);
+
+kct_status kct_cgls(const kct_plan *plan, const float *d_b, float *d_x, int32_t warm_start, int32_t max_iter,
+                    double tol, void *d_work, size_t work_bytes, double *h_normal, double *h_data,
+                    kct_cgls_report *report, void *stream);
 
 /* Static description of a status code. */
 const char *kct_status_string(kct_status status);

@@ -35,7 +35,9 @@ constexpr int NTHREADS = 32 * NWARP;
 constexpr int EV_CAP = 64;         // crossing events queued per warp and round
 constexpr int KCT_ROWS = 32;       // row boundaries of one voxel (its footprint spans <= 31 rows)
 constexpr int TILE_CAP = 8192;     // floats of the shared detector tile
-constexpr int VIEW_CHUNK = 16;     // views per forward block
+constexpr int VIEW_CHUNK = 16;     // default views per forward block (a plan may tune it)
+constexpr int MAX_VIEW_CHUNK = 64; // largest views per forward block a plan accepts
+constexpr int TUNE_VIEWS = 64;     // views the forward tuning launches cover
 constexpr unsigned FULLMASK = 0xffffffffu;
 
 struct WarpSmem {
@@ -472,7 +474,8 @@ __device__ __forceinline__ void brick_origin(const Grid& G, int& i0, int& j0) {
 // Kernels
 // ---------------------------------------------------------------------------------------
 
-// Forward projection. grid: (bricks in x1 x2, segments along x3, view chunks x batch).
+// Forward projection. grid: (bricks in x1 x2, segments along x3, view chunks x batch), a
+// chunk being view_chunk consecutive views.
 // Volume b of the batch starts at vol + b * vstride, its projections at out + b * pstride.
 // SCALING 0 / 1 multiplies by the cos / exact pixel factor while the tile is flushed;
 // SCALING < 0 leaves the unscaled sums of Eq. cvpsu. out must be zeroed (or hold the values
@@ -481,7 +484,8 @@ __device__ __forceinline__ void brick_origin(const Grid& G, int& i0, int& j0) {
 template <int VARIANT, int SCALING>
 __global__ void __launch_bounds__(NTHREADS, 2) fwd_kernel(const View* __restrict__ views, Grid G,
                                                           const float* __restrict__ vol, float* __restrict__ out,
-                                                          long long vstride, long long pstride, int* err) {
+                                                          long long vstride, long long pstride, int view_chunk,
+                                                          int* err) {
     extern __shared__ float dyn[];
     __shared__ BlockSmem bs;
     float* mu_s = dyn;
@@ -490,7 +494,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) fwd_kernel(const View* __restrict
     int i0, j0;
     brick_origin(G, i0, j0);
     const int kbase = blockIdx.y * SEG;
-    const int nchunk = (G.nviews + VIEW_CHUNK - 1) / VIEW_CHUNK;
+    const int nchunk = (G.nviews + view_chunk - 1) / view_chunk;
     const int chunk = blockIdx.z % nchunk, batch = blockIdx.z / nchunk;
     vol += batch * vstride;
     out += batch * pstride;
@@ -499,8 +503,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) fwd_kernel(const View* __restrict
         const int i = i0 + c % BX, j = j0 + c / BX, k = kbase + kk;
         mu_s[q] = (i < G.nx && j < G.ny && k < G.nz) ? __ldg(&vol[((size_t)k * G.ny + j) * G.nx + i]) : 0.f;
     }
-    const int v_end = min((chunk + 1) * VIEW_CHUNK, G.nviews);
-    for (int view = chunk * VIEW_CHUNK; view < v_end; ++view) {
+    const int v_end = min((chunk + 1) * view_chunk, G.nviews);
+    for (int view = chunk * view_chunk; view < v_end; ++view) {
         __syncthreads();
         if (threadIdx.x == 0) {
             bs.V = views[view];

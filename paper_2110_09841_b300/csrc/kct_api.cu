@@ -2,6 +2,7 @@
 // kernel launches. See include/kct.h for the contract of every entry point.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -13,6 +14,7 @@
 #include "kct.h"
 #include "cvp_device.cuh"
 #include "cvp_kernels.cuh"
+#include "cgls_kernels.cuh"
 
 using kct::Grid;
 using kct::View;
@@ -29,6 +31,7 @@ struct kct_plan {
     View* d_views;
     int* d_err;
     unsigned long long* d_count;
+    int fwd_chunk;                 // views per forward block (kct_plan_autotune may change it)
 };
 
 namespace {
@@ -193,15 +196,32 @@ cudaError_t brick_kernel_attributes() {
     return done;
 }
 
-unsigned view_chunks(const Grid& G) { return (unsigned)((G.nviews + kct::VIEW_CHUNK - 1) / kct::VIEW_CHUNK); }
+unsigned view_chunks(const Grid& G, int chunk) { return (unsigned)((G.nviews + chunk - 1) / chunk); }
+
+// Forward launch over the views of G (the plan's grid, or the same grid cut to its first
+// views when tuning) with `chunk` views per block.
+template <int VARIANT, int SCALING>
+void launch_fwd_grid(const kct_plan* p, const Grid& G, int chunk, const float* vol, float* out, int nbatch,
+                     cudaStream_t st) {
+    dim3 grid(bricks(G), segments(G), view_chunks(G, chunk) * (unsigned)nbatch);
+    const long long vs = (long long)G.nx * G.ny * G.nz, ps = (long long)G.nu * G.nv * G.nviews;
+    kct::fwd_kernel<VARIANT, SCALING><<<grid, kct::NTHREADS, kBrickDynSmem, st>>>(p->d_views, G, vol, out, vs, ps,
+                                                                                   chunk, p->d_err);
+}
 
 template <int VARIANT, int SCALING>
 void launch_fwd(const kct_plan* p, const float* vol, float* out, int nbatch, cudaStream_t st) {
-    const Grid& G = p->grid;
-    dim3 grid(bricks(G), segments(G), view_chunks(G) * (unsigned)nbatch);
-    const long long vs = (long long)G.nx * G.ny * G.nz, ps = (long long)G.nu * G.nv * G.nviews;
-    kct::fwd_kernel<VARIANT, SCALING><<<grid, kct::NTHREADS, kBrickDynSmem, st>>>(p->d_views, G, vol, out, vs, ps,
-                                                                                   p->d_err);
+    launch_fwd_grid<VARIANT, SCALING>(p, p->grid, p->fwd_chunk, vol, out, nbatch, st);
+}
+
+void launch_fwd_any(const kct_plan* p, const Grid& G, int chunk, const float* vol, float* out, cudaStream_t st) {
+    const int key = (p->variant == KCT_CVP_RELAXED ? 2 : 0) + (p->scaling == KCT_SCALE_EXACT ? 1 : 0);
+    switch (key) {
+        case 0: launch_fwd_grid<0, 0>(p, G, chunk, vol, out, 1, st); break;
+        case 1: launch_fwd_grid<0, 1>(p, G, chunk, vol, out, 1, st); break;
+        case 2: launch_fwd_grid<1, 0>(p, G, chunk, vol, out, 1, st); break;
+        default: launch_fwd_grid<1, 1>(p, G, chunk, vol, out, 1, st); break;
+    }
 }
 
 template <int VARIANT, int SCALING>
@@ -287,6 +307,7 @@ kct_status kct_plan_create(kct_plan** out, const kct_volume_desc* vol, const kct
     p->d_views = nullptr;
     p->d_err = nullptr;
     p->d_count = nullptr;
+    p->fwd_chunk = kct::VIEW_CHUNK;
     p->h_views.resize(nviews);
     for (int q = 0; q < nviews; ++q) {
         std::string why = setup_view(pmats + 12 * q, *vol, p->h_views[q]);
@@ -352,7 +373,8 @@ static kct_status project_impl(const kct_plan* p, const float* d_vol, float* d_p
     if (!d_vol || !d_proj) return fail(KCT_ERR_INVALID_ARG, "null data pointer");
     if (nbatch <= 0) return fail(KCT_ERR_INVALID_ARG, "nbatch must be positive");
     const Grid& G = p->grid;
-    if ((long long)view_chunks(G) * nbatch > 65535) return fail(KCT_ERR_UNSUPPORTED, "batch too large for one launch");
+    if ((long long)view_chunks(G, p->fwd_chunk) * nbatch > 65535)
+        return fail(KCT_ERR_UNSUPPORTED, "batch too large for one launch");
     if ((s = set_device(p)) != KCT_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     size_t pbytes = sizeof(float) * (size_t)G.nu * G.nv * G.nviews * nbatch;
@@ -412,6 +434,65 @@ kct_status kct_backproject_batch(const kct_plan* p, const float* d_proj, int32_t
     return backproject_impl(p, d_proj, d_vol, nbatch, accumulate, stream);
 }
 
+kct_status kct_plan_set_view_chunk(kct_plan* p, int32_t chunk) {
+    kct_status s = check_plan(p);
+    if (s != KCT_OK) return s;
+    if (chunk < 1 || chunk > kct::MAX_VIEW_CHUNK) return fail(KCT_ERR_INVALID_ARG, "view chunk outside [1, 64]");
+    p->fwd_chunk = chunk;
+    return KCT_OK;
+}
+
+kct_status kct_plan_get_view_chunk(const kct_plan* p, int32_t* chunk) {
+    kct_status s = check_plan(p);
+    if (s != KCT_OK) return s;
+    if (!chunk) return fail(KCT_ERR_INVALID_ARG, "null output pointer");
+    *chunk = p->fwd_chunk;
+    return KCT_OK;
+}
+
+kct_status kct_plan_autotune(kct_plan* p, const float* d_vol, float* d_proj, int32_t* chunk, float* ms,
+                             void* stream) {
+    kct_status s = check_plan(p);
+    if (s != KCT_OK) return s;
+    if (!d_vol || !d_proj) return fail(KCT_ERR_INVALID_ARG, "null data pointer");
+    if ((s = set_device(p)) != KCT_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    Grid G = p->grid;
+    G.nviews = std::min(G.nviews, kct::TUNE_VIEWS);
+    const size_t pbytes = sizeof(float) * (size_t)G.nu * G.nv * G.nviews;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    static const int kCand[] = {1, 2, 4, 8, 16, 32, 64};
+    int best = p->fwd_chunk;
+    float best_ms = -1.f;
+    for (int ci = 0; ci < 7 && e == cudaSuccess; ++ci) {
+        const int c = kCand[ci];
+        if (c > kct::MAX_VIEW_CHUNK || (c > G.nviews && c != 1)) break;
+        float t = 0.f;
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {   // the first run is a warm-up
+            e = cudaMemsetAsync(d_proj, 0, pbytes, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+            if (e == cudaSuccess) launch_fwd_any(p, G, c, d_vol, d_proj, st);
+            if (e == cudaSuccess) e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        }
+        if (e == cudaSuccess && (best_ms < 0.f || t < best_ms)) {
+            best_ms = t;
+            best = c;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune");
+    p->fwd_chunk = best;
+    if (chunk) *chunk = best;
+    if (ms) *ms = best_ms;
+    return KCT_OK;
+}
+
 kct_status kct_pixel_factors(const kct_plan* p, float* d_out, void* stream) {
     kct_status s = check_plan(p);
     if (s != KCT_OK) return s;
@@ -461,6 +542,127 @@ kct_status kct_last_device_error(const kct_plan* p, int32_t* code, void* stream)
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
     *code = h;
+    return KCT_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// CGLS
+// ---------------------------------------------------------------------------------------
+
+namespace {
+
+struct CglsLayout {
+    size_t r, q, s, p, part, sc, total;
+};
+
+size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
+
+CglsLayout cgls_layout(const Grid& G) {
+    const size_t nproj = (size_t)G.nu * G.nv * G.nviews, nvol = (size_t)G.nx * G.ny * G.nz;
+    CglsLayout L;
+    L.r = 0;
+    L.q = L.r + align256(nproj * sizeof(float));
+    L.s = L.q + align256(nproj * sizeof(float));
+    L.p = L.s + align256(nvol * sizeof(float));
+    L.part = L.p + align256(nvol * sizeof(float));
+    L.sc = L.part + align256(3 * kct::VEC_MAX_BLOCKS * sizeof(double));
+    L.total = L.sc + align256(sizeof(kct::CglsScalars));
+    return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t kct_cgls_workspace_bytes(const kct_plan* p) { return p ? cgls_layout(p->grid).total : 0; }
+
+kct_status kct_cgls(const kct_plan* p, const float* d_b, float* d_x, int32_t warm_start, int32_t max_iter,
+                    double tol, void* d_work, size_t work_bytes, double* h_normal, double* h_data,
+                    kct_cgls_report* report, void* stream) {
+    kct_status s = check_plan(p);
+    if (s != KCT_OK) return s;
+    if (!d_b || !d_x || !d_work) return fail(KCT_ERR_INVALID_ARG, "null data pointer");
+    if (max_iter < 0 || !(tol >= 0.0)) return fail(KCT_ERR_INVALID_ARG, "max_iter and tol must be >= 0");
+    const Grid& G = p->grid;
+    const CglsLayout L = cgls_layout(G);
+    if (work_bytes < L.total) return fail(KCT_ERR_INVALID_ARG, "workspace smaller than kct_cgls_workspace_bytes");
+    if (((uintptr_t)d_work & 255) || ((uintptr_t)d_b & 15) || ((uintptr_t)d_x & 15))
+        return fail(KCT_ERR_INVALID_ARG, "d_work must be 256-byte and d_b, d_x 16-byte aligned");
+    if ((s = set_device(p)) != KCT_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    int sms = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    const int nb = std::min(kct::VEC_MAX_BLOCKS, std::max(1, 8 * sms));
+    const long long nproj = (long long)G.nu * G.nv * G.nviews, nvol = (long long)G.nx * G.ny * G.nz;
+    unsigned char* w = (unsigned char*)d_work;
+    float* r = (float*)(w + L.r);
+    float* q = (float*)(w + L.q);
+    float* sv = (float*)(w + L.s);
+    float* pv = (float*)(w + L.p);
+    double* part_qq = (double*)(w + L.part);
+    double* part_ss = part_qq + kct::VEC_MAX_BLOCKS;
+    double* part_rr = part_ss + kct::VEC_MAX_BLOCKS;
+    kct::CglsScalars* sc = (kct::CglsScalars*)(w + L.sc);
+    const int T = kct::VEC_THREADS;
+
+    // start: r = b - A x0, s = A^T r, p = s, gamma_0 = |s|^2, plus |b|^2 and |A^T b|^2
+    kct::sumsq_kernel<<<nb, T, 0, st>>>(d_b, nproj, part_rr);
+    kct::store_sum_kernel<<<1, T, 0, st>>>(part_rr, nb, &sc->bb2);
+    if (warm_start) {
+        if ((s = backproject_impl(p, d_b, sv, 1, 0, st)) != KCT_OK) return s;
+        kct::sumsq_kernel<<<nb, T, 0, st>>>(sv, nvol, part_ss);
+        kct::store_sum_kernel<<<1, T, 0, st>>>(part_ss, nb, &sc->atb2);
+        if ((s = project_impl(p, d_x, q, 1, 0, st)) != KCT_OK) return s;
+        kct::residual_kernel<<<nb, T, 0, st>>>(d_b, q, r, nproj, part_rr);
+        if ((s = backproject_impl(p, r, sv, 1, 0, st)) != KCT_OK) return s;
+        kct::sumsq_kernel<<<nb, T, 0, st>>>(sv, nvol, part_ss);
+    } else {
+        e = cudaMemsetAsync(d_x, 0, sizeof(float) * nvol, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(r, d_b, sizeof(float) * nproj, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "CGLS start");
+        if ((s = backproject_impl(p, r, sv, 1, 0, st)) != KCT_OK) return s;
+        kct::sumsq_kernel<<<nb, T, 0, st>>>(sv, nvol, part_ss);
+        kct::store_sum_kernel<<<1, T, 0, st>>>(part_ss, nb, &sc->atb2);
+    }
+    kct::cgls_p_kernel<<<nb, T, 0, st>>>(sv, pv, nvol, part_ss, part_rr, nb, nullptr, &sc->gamma[0], sc);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "CGLS start kernels");
+
+    auto read_residuals = [&](double* out2) -> kct_status {
+        cudaError_t e2 = cudaMemcpyAsync(out2, &sc->normal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
+        return e2 == cudaSuccess ? KCT_OK : cuda_fail(e2, "CGLS residual read");
+    };
+    double res[2] = {0.0, 0.0};
+    if ((s = read_residuals(res)) != KCT_OK) return s;
+    if (h_normal) h_normal[0] = res[0];
+    if (h_data) h_data[0] = res[1];
+    int k = 0;
+    while (k < max_iter && !(res[0] <= tol)) {
+        double* g_cur = &sc->gamma[k & 1];
+        double* g_next = &sc->gamma[(k + 1) & 1];
+        if ((s = project_impl(p, pv, q, 1, 0, st)) != KCT_OK) return s;
+        kct::sumsq_kernel<<<nb, T, 0, st>>>(q, nproj, part_qq);
+        kct::cgls_xr_kernel<<<nb, T, 0, st>>>(d_x, pv, nvol, r, q, nproj, part_qq, nb, g_cur, part_rr);
+        if ((s = backproject_impl(p, r, sv, 1, 0, st)) != KCT_OK) return s;
+        kct::sumsq_kernel<<<nb, T, 0, st>>>(sv, nvol, part_ss);
+        kct::cgls_p_kernel<<<nb, T, 0, st>>>(sv, pv, nvol, part_ss, part_rr, nb, g_cur, g_next, sc);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "CGLS step kernels");
+        if ((s = read_residuals(res)) != KCT_OK) return s;
+        ++k;
+        if (h_normal) h_normal[k] = res[0];
+        if (h_data) h_data[k] = res[1];
+    }
+    if (report) {
+        report->iterations = k;
+        report->converged = res[0] <= tol ? 1 : 0;
+        report->normal_residual = res[0];
+        report->data_residual = res[1];
+    }
     return KCT_OK;
 }
 
@@ -570,9 +772,9 @@ extern "C" kct_status kct_project_static(const kct_volume_desc* vol, const kct_d
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     dim3 grid(bricks(G), segments(G), (unsigned)((G.nviews + kct::VIEW_CHUNK - 1) / kct::VIEW_CHUNK));
     if (variant == KCT_CVP_RELAXED)
-        kct::fwd_kernel<1, -1><<<grid, kct::NTHREADS, kBrickDynSmem, st>>>(d_views, G, d_vol, S, 0, 0, d_err);
+        kct::fwd_kernel<1, -1><<<grid, kct::NTHREADS, kBrickDynSmem, st>>>(d_views, G, d_vol, S, 0, 0, kct::VIEW_CHUNK, d_err);
     else
-        kct::fwd_kernel<0, -1><<<grid, kct::NTHREADS, kBrickDynSmem, st>>>(d_views, G, d_vol, S, 0, 0, d_err);
+        kct::fwd_kernel<0, -1><<<grid, kct::NTHREADS, kBrickDynSmem, st>>>(d_views, G, d_vol, S, 0, 0, kct::VIEW_CHUNK, d_err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "forward projection launch");
     dim3 sgrid((unsigned)(((long)G.nu * G.nv + 255) / 256), G.nviews);

@@ -138,10 +138,15 @@ WORKLOADS = {
     "pfeiffer2021": dict(n=(256, 256, 256), a=(0.5, 0.5, 0.5), det=(1280, 960), pitch=(0.25, 0.25),
                          nviews=100, sid=750.0, sdd=1000.0, arc_deg=198.0,
                          phantom=dict(count=40, semi=(3.0, 30.0), mu=(0.0, 0.03))),
+    # CGLS reconstruction problem: 128^3 @ 0.5 mm, 180 views / 360 deg, SID 750 / SDD 1200,
+    # 256x192 detector @ 0.8 mm; data with Poisson noise at 1e5 photons per pixel
+    "cgls128": dict(n=(128, 128, 128), a=(0.5, 0.5, 0.5), det=(256, 192), pitch=(0.8, 0.8),
+                    nviews=180, sid=750.0, sdd=1200.0, arc_deg=360.0,
+                    phantom=dict(count=20, semi=(3.0, 16.0), mu=(0.005, 0.02))),
 }
 
 WORKLOAD_SEEDS = {"cvp32": 1001, "cvp256": 1002, "cvp512": 1003, "cvp512wide": 1003,
-                  "long2010": 1011, "pfeiffer2021": 1012}
+                  "long2010": 1011, "pfeiffer2021": 1012, "cgls128": 1013}
 
 
 def workload_geometry(name: str) -> Geometry:
@@ -262,6 +267,18 @@ def perfusion_frames(geom: Geometry, seed: int, frames: int = 8, device="cpu"):
             fr += masks[v] * float(amp[v] * math.exp(-((f - t0[v]) ** 2) / (2 * sig[v] ** 2)))
         out[f] = fr
     return out
+
+
+def poisson_log_data(clean, photons: float, seed: int):
+    """Noisy line integrals from noise-free ones (Beer-Lambert with Poisson counts):
+    b = -ln(max(N, 1) / I0), N ~ Poisson(I0 exp(-clean)), seeded; same device as `clean`."""
+    import torch
+
+    g = torch.Generator(device=clean.device)
+    g.manual_seed(seed)
+    lam = photons * torch.exp(-clean.double())
+    counts = torch.poisson(lam, generator=g).clamp_(min=1.0)
+    return (-torch.log(counts / photons)).to(torch.float32)
 
 
 def uniform_projections(shape, seed: int, device="cpu"):

@@ -25,7 +25,8 @@ STATUS = {0: "KCT_OK", 1: "KCT_ERR_INVALID_ARG", 2: "KCT_ERR_GEOMETRY", 3: "KCT_
 EXPORTED = ["kct_plan_create", "kct_plan_destroy", "kct_project", "kct_backproject",
             "kct_pixel_factors", "kct_count_pairs", "kct_last_device_error", "kct_status_string",
             "kct_last_error_message", "kct_version", "kct_project_static", "kct_project_batch",
-            "kct_backproject_batch"]
+            "kct_backproject_batch", "kct_cgls_workspace_bytes", "kct_cgls", "kct_plan_autotune",
+            "kct_plan_set_view_chunk", "kct_plan_get_view_chunk"]
 
 
 class KctError(RuntimeError):
@@ -42,6 +43,11 @@ class VolumeDesc(ctypes.Structure):
 class DetectorDesc(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_int32), ("nv", ctypes.c_int32),
                 ("pu", ctypes.c_double), ("pv", ctypes.c_double)]
+
+
+class CglsReport(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("normal_residual", ctypes.c_double), ("data_residual", ctypes.c_double)]
 
 
 _lib = None
@@ -85,6 +91,17 @@ def load(path: str | None = None):
         lib.kct_project_static.argtypes = [ctypes.POINTER(VolumeDesc), ctypes.POINTER(DetectorDesc), V, I32, I, I,
                                            V, V, I32, V]
         lib.kct_project_static.restype = I
+        lib.kct_plan_autotune.argtypes = [V, V, V, ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_float), V]
+        lib.kct_plan_autotune.restype = I
+        lib.kct_plan_set_view_chunk.argtypes = [V, I32]
+        lib.kct_plan_set_view_chunk.restype = I
+        lib.kct_plan_get_view_chunk.argtypes = [V, ctypes.POINTER(I32)]
+        lib.kct_plan_get_view_chunk.restype = I
+        lib.kct_cgls_workspace_bytes.argtypes = [V]
+        lib.kct_cgls_workspace_bytes.restype = ctypes.c_size_t
+        lib.kct_cgls.argtypes = [V, V, V, I32, I32, ctypes.c_double, V, ctypes.c_size_t, V, V,
+                                 ctypes.POINTER(CglsReport), V]
+        lib.kct_cgls.restype = I
         _lib = lib
     return _lib
 
@@ -205,6 +222,66 @@ class Projector:
         _check(self.lib.kct_backproject_batch(self._h, yp, B, _dev_ptr(out, (B,) + g.vol_shape, "out"),
                                               int(bool(accumulate)), _stream_handle(stream)))
         return out
+
+    def autotune(self, x, scratch=None, stream=None):
+        """Pick the forward kernel's views per block by timing (kct_plan_autotune) on volume x.
+        Returns (chunk, forward ms over the first min(nviews, 64) views)."""
+        import torch
+
+        g = self.geom
+        xp = _dev_ptr(x, g.vol_shape, "x")
+        if scratch is None:
+            scratch = torch.empty(g.proj_shape, dtype=torch.float32, device=x.device)
+        c = ctypes.c_int32(0)
+        ms = ctypes.c_float(0.0)
+        _check(self.lib.kct_plan_autotune(self._h, xp, _dev_ptr(scratch, g.proj_shape, "scratch"), ctypes.byref(c),
+                                          ctypes.byref(ms), _stream_handle(stream)))
+        return int(c.value), float(ms.value)
+
+    @property
+    def view_chunk(self) -> int:
+        c = ctypes.c_int32(0)
+        _check(self.lib.kct_plan_get_view_chunk(self._h, ctypes.byref(c)))
+        return int(c.value)
+
+    @view_chunk.setter
+    def view_chunk(self, chunk: int):
+        _check(self.lib.kct_plan_set_view_chunk(self._h, int(chunk)))
+
+    def cgls_workspace(self):
+        """Device scratch for cgls(): a uint8 CUDA tensor of kct_cgls_workspace_bytes."""
+        import torch
+
+        return torch.empty(int(self.lib.kct_cgls_workspace_bytes(self._h)), dtype=torch.uint8, device="cuda")
+
+    def cgls(self, b, x0=None, max_iter=100, tol=1e-3, out=None, workspace=None, stream=None):
+        """CGLS for min |b - A x| (kct_cgls): from x0 (warm start) or from 0, until the
+        normal-equation residual |A^T(b - A x)| / |A^T b| <= tol or max_iter steps.
+        Returns (x, info) with info = dict(iterations, converged, normal, data); normal and
+        data are the residual histories (entry k after k steps)."""
+        import torch
+
+        g = self.geom
+        bp = _dev_ptr(b, g.proj_shape, "b")
+        if out is None:
+            out = torch.empty(g.vol_shape, dtype=torch.float32, device=b.device)
+        xp = _dev_ptr(out, g.vol_shape, "out")
+        if x0 is not None:
+            _dev_ptr(x0, g.vol_shape, "x0")
+            if x0.data_ptr() != out.data_ptr():
+                out.copy_(x0)
+        if workspace is None:
+            workspace = self.cgls_workspace()
+        hn = np.zeros(max_iter + 1)
+        hd = np.zeros(max_iter + 1)
+        rep = CglsReport()
+        _check(self.lib.kct_cgls(self._h, bp, xp, int(x0 is not None), int(max_iter), float(tol),
+                                 ctypes.c_void_p(workspace.data_ptr()), int(workspace.numel()),
+                                 hn.ctypes.data_as(ctypes.c_void_p), hd.ctypes.data_as(ctypes.c_void_p),
+                                 ctypes.byref(rep), _stream_handle(stream)))
+        k = int(rep.iterations)
+        return out, dict(iterations=k, converged=bool(rep.converged), normal=hn[:k + 1].copy(),
+                         data=hd[:k + 1].copy())
 
     def pixel_factors(self, stream=None):
         import torch

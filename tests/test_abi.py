@@ -64,6 +64,12 @@ def test_rejects_invalid_arguments(lib):
     assert lib.kct_project(None, None, None, 0, None) == 1
     assert lib.kct_backproject(None, None, None, 0, None) == 1
     assert lib.kct_plan_destroy(None) == 0
+    assert lib.kct_project_batch(None, None, 1, None, 0, None) == 1
+    assert lib.kct_backproject_batch(None, None, 1, None, 0, None) == 1
+    assert lib.kct_plan_set_view_chunk(None, 4) == 1
+    assert lib.kct_plan_autotune(None, None, None, None, None, None) == 1
+    assert lib.kct_cgls_workspace_bytes(None) == 0
+    assert lib.kct_cgls(None, None, None, 0, 1, 1e-3, None, 0, None, None, None, None) == 1
 
 
 def test_rejects_geometry_outside_the_arrangement(lib):

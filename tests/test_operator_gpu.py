@@ -113,3 +113,20 @@ def test_captured_graph_replays():
         rb, rx = A.project(x), A.backproject(y)
         torch.testing.assert_close(b, rb, rtol=1e-5, atol=1e-6 * float(rb.abs().max()))
         torch.testing.assert_close(xb, rx, rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("vname", ["exact", "relaxed"])
+def test_autotuned_chunk_gives_the_same_projection(vname):
+    g = inputs.workload_geometry("cvp32")
+    x = inputs.workload_phantom("cvp32").cuda()
+    A = Projector(g, vname, "cos")
+    assert A.view_chunk == 16
+    ref = A.project(x)
+    chunk, ms = A.autotune(x)
+    assert chunk in (1, 2, 4, 8, 16, 32, 64) and ms > 0 and A.view_chunk == chunk
+    for c in (1, 5, 64):
+        A.view_chunk = c
+        torch.testing.assert_close(A.project(x), ref, rtol=1e-5, atol=1e-6 * float(ref.abs().max()))
+    from paper_2110_09841_b300.kct import KctError
+    with pytest.raises(KctError):
+        A.view_chunk = 65
