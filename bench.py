@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--scaling", default="cos", choices=["cos", "exact"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cgls", action="store_true")
+    ap.add_argument("--paper-geometries", action="store_true",
+                    help="time P and BP at the geometries of the paper's Tables I and II and exit")
     ap.add_argument("--cgls-max-iter", type=int, default=200)
     ap.add_argument("--profile-case", default=None, metavar="WORKLOAD",
                     help="run one projector call on a sub-sampled workload (for ncu captures) and exit")
@@ -175,6 +177,21 @@ class ClockSampler:
         load = [v for v in sm if mx and v > 0.3 * mx] or sm
         return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": reasons,
                 "samples": len(rows), "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+def probe_fp32_tflops():
+    """FP32 FMA throughput measured on this GPU by the probe kernel (2 FLOP per FMA)."""
+    import ctypes
+
+    from paper_2110_09841_b300 import build
+
+    lib = ctypes.CDLL(build.PROBE_LIB)
+    lib.kct_probe_fp32.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_float)]
+    lib.kct_probe_fp32.restype = ctypes.c_int
+    flops, ms = ctypes.c_double(0.0), ctypes.c_float(0.0)
+    rc = lib.kct_probe_fp32(8, 20000, ctypes.byref(flops), ctypes.byref(ms))
+    return flops.value / 1e12 if rc == 0 else None
 
 
 def measured_peaks():
@@ -348,6 +365,7 @@ def run_kct(args):
         p = per[v]
         p["p_bp_gvv_s"] = geom.voxel_views / ((p["project_ms"] + p["backproject_ms"]) / 1e3) / 1e9
         p["nnz_pairs"] = ops[v].count_pairs()
+        p["nnz_pairs_per_s_p_bp"] = 2 * p["nnz_pairs"] / ((p["project_ms"] + p["backproject_ms"]) / 1e3)
 
     # end to end through the public API from pinned host buffers, copies inside the timed region
     e2e = None
@@ -403,11 +421,13 @@ def run_kct(args):
     flop_vv = NCU[name]["flop_per_vv"] if args.workload == WORKLOAD else None
     achieved = (flop_vv * geom.voxel_views / (dom_ms / 1e3) / 1e12) if flop_vv else None
     traffic = full_launch_traffic(name, geom.nviews) if args.workload == WORKLOAD else None
+    fp32_probe = probe_fp32_tflops()
     roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "measured_fp32_fma_tflops": fp32_probe,
                 "frac": (achieved / peak_tflops) if achieved else None, "traffic": traffic,
                 "traffic_unit": "bytes per launch (ncu, 8-view capture scaled to the full launch)",
                 "launch_ms": dom_ms, "flop_per_voxel_view": flop_vv,
-                "peak_basis": f"FP32 FMA: {sms} SMs x 128 lanes x 2 FLOP x {max_mhz:.0f} MHz (derived, no measured FP32 peak)"}
+                "peak_basis": f"FP32 FMA: {sms} SMs x 128 lanes x 2 FLOP x {max_mhz:.0f} MHz (derived; measured_fp32_fma_tflops is the probe kernel at the running clock)"}
 
     cb_val, cb_desc, cb_threads = cpu_baseline(geom, 10.0)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -429,10 +449,60 @@ def run_kct(args):
         dist.destroy_process_group()
 
 
+# The paper's own projector timings at its Table I / II geometries (Gvoxel-views/s from its
+# per-call seconds; Radeon VII, FP64 near-exact with elevation correction, FP32 relaxed).
+PAPER_GVV_S = {
+    "long2010": {"exact": {"project": 0.615, "backproject": 1.226}, "relaxed": {"project": 1.964, "backproject": 4.646},
+                 "source": "Sec. IV-A Table I, AMD Radeon VII"},
+    "pfeiffer2021": {"exact": {"project": 0.0746, "backproject": 0.1190},
+                     "relaxed": {"project": 0.224, "backproject": 0.409},
+                     "source": "Sec. IV-A Table II, AMD Radeon VII"},
+}
+
+
+def run_paper_geometries(args):
+    """P and BP of both variants at the paper's Table I and II geometries (one warm-up and
+    one timed call each, CUDA events), next to the paper's published throughput."""
+    import torch
+
+    from paper_2110_09841_b300 import build, inputs
+    from paper_2110_09841_b300.kct import Projector
+
+    build.build()
+    out = {"mode": "paper geometries", "unit": UNIT, "scaling": args.scaling, "results": {}}
+    for name in ("long2010", "pfeiffer2021"):
+        g = inputs.workload_geometry(name)
+        x = inputs.workload_phantom(name, device="cuda")
+        y = inputs.uniform_projections(g.proj_shape, 2024, device="cuda")
+        res = {"voxel_views": g.voxel_views, "paper": PAPER_GVV_S[name]}
+        for v in ("exact", "relaxed"):
+            A = Projector(g, v, args.scaling)
+            b = torch.empty(g.proj_shape, device="cuda")
+            xb = torch.empty(g.vol_shape, device="cuda")
+            r = {}
+            for d, call in (("project", lambda: A.project(x, out=b)), ("backproject", lambda: A.backproject(y, out=xb))):
+                call()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                call()
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                r[d] = {"ms": ms, "gvv_s": g.voxel_views / (ms / 1e3) / 1e9,
+                        "x_paper": g.voxel_views / (ms / 1e3) / 1e9 / PAPER_GVV_S[name][v][d]}
+            r["nnz_pairs"] = A.count_pairs()
+            res[v] = r
+        out["results"][name] = res
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.profile_case:
         run_profile_case(args)
+    elif args.paper_geometries:
+        run_paper_geometries(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

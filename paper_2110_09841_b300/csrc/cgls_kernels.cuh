@@ -166,20 +166,25 @@ __global__ void __launch_bounds__(VEC_THREADS) cgls_p_kernel(const float* __rest
     const double ss = sum_partials(part_ss, nb, sh);
     const double go = gamma_old ? *gamma_old : 0.0;
     const float beta = go > 0.0 ? (float)(ss / go) : 0.0f;
+    // at the start p holds whatever the workspace held (possibly NaN): p = s without reading it
+    const bool keep = beta != 0.0f;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long v4 = nvol >> 2;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < v4; i += stride) {
         const float4 sv = __ldcs(reinterpret_cast<const float4*>(s) + i);
-        float4 pv = reinterpret_cast<float4*>(p)[i];
-        pv.x = fmaf(beta, pv.x, sv.x);
-        pv.y = fmaf(beta, pv.y, sv.y);
-        pv.z = fmaf(beta, pv.z, sv.z);
-        pv.w = fmaf(beta, pv.w, sv.w);
+        float4 pv = sv;
+        if (keep) {
+            pv = reinterpret_cast<float4*>(p)[i];
+            pv.x = fmaf(beta, pv.x, sv.x);
+            pv.y = fmaf(beta, pv.y, sv.y);
+            pv.z = fmaf(beta, pv.z, sv.z);
+            pv.w = fmaf(beta, pv.w, sv.w);
+        }
         reinterpret_cast<float4*>(p)[i] = pv;
     }
     if (blockIdx.x == 0 && threadIdx.x < (nvol & 3)) {
         const long long i = 4 * v4 + threadIdx.x;
-        p[i] = fmaf(beta, p[i], s[i]);
+        p[i] = keep ? fmaf(beta, p[i], s[i]) : s[i];
     }
     if (blockIdx.x == 0) {
         const double rr = sum_partials(part_rr, nb, sh);

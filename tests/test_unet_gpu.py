@@ -1,0 +1,54 @@
+"""The warm-start U-Net on the tensor-core convolutions against the FP64 oracle network.
+
+The GPU network keeps activations in bf16 (each layer's output rounded to 2^-9 relative),
+so its output and gradients differ from the FP64 network by the accumulated bf16 rounding of
+about 20 layers: a few 1e-3 relative. The checks allow 3e-2 relative (L2) and a cosine
+similarity of at least 0.999; a wrong kernel, layout or flipped tap gives O(1) errors.
+"""
+import pytest
+import torch
+
+import oracle.unet as ounet
+from paper_2110_09841_b300.unet import UNet3D
+
+pytestmark = pytest.mark.gpu
+
+SHAPE = (1, 8, 64, 128)     # n, d, h, w: the smallest volume whose coarsest level (1 x 8 x 16) the kernels take
+
+
+def rel(a, b):
+    return float((a - b).norm() / b.norm())
+
+
+def cos(a, b):
+    return float((a * b).sum() / (a.norm() * b.norm()))
+
+
+def test_forward_and_gradients_match_oracle():
+    model = UNet3D(seed=3).cuda()
+    with torch.no_grad():                          # give the head nonzero weights so every layer gets gradient
+        model.head_w.normal_(0.0, 0.05, generator=torch.Generator(device="cuda").manual_seed(1))
+    g = torch.Generator().manual_seed(7)
+    inp = torch.rand(SHAPE, generator=g)
+    target = torch.rand(SHAPE, generator=g)
+    out = model(inp.cuda())
+    loss = torch.mean((out - target.cuda()) ** 2)
+    loss.backward()
+
+    # the oracle gets the bf16-rounded weights the GPU network used
+    p = {name: t.detach().cpu().double() for name, t in model.named_parameters()}
+    for n in model.names:
+        p[n + "_w"] = model.get_parameter(n + "_w").detach().to(torch.bfloat16).cpu().double().requires_grad_(True)
+        p[n + "_b"] = p[n + "_b"].requires_grad_(True)
+    ref = ounet.forward(p, inp.double())
+    rloss = torch.mean((ref - target.double()) ** 2)
+    rloss.backward()
+    assert rel(out.detach().cpu().double(), ref.detach()) < 3e-2
+    for n in model.names:
+        for suffix in ("_w", "_b"):
+            gg = model.get_parameter(n + suffix).grad.cpu().double()
+            rg = p[n + suffix].grad
+            if rg.norm() == 0:
+                continue
+            assert rel(gg, rg) < 3e-2, (n + suffix, rel(gg, rg))
+            assert cos(gg, rg) > 0.999, (n + suffix, cos(gg, rg))
