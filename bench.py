@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--scaling", default="cos", choices=["cos", "exact"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cgls", action="store_true")
+    ap.add_argument("--convs", action="store_true",
+                    help="time the warm-start U-Net's tensor-core convolutions at 128^3 and exit")
     ap.add_argument("--paper-geometries", action="store_true",
                     help="time P and BP at the geometries of the paper's Tables I and II and exit")
     ap.add_argument("--cgls-max-iter", type=int, default=200)
@@ -497,10 +499,52 @@ def run_paper_geometries(args):
     print(json.dumps(out), flush=True)
 
 
+def run_convs(args):
+    """Forward, input-gradient and weight-gradient convolutions of every layer shape of the
+    warm-start U-Net at 128^3 (CUDA events, 2 warm-up and 5 timed calls each), as TFLOP/s
+    against the measured BF16 dense peak."""
+    import torch
+
+    from paper_2110_09841_b300 import build, conv
+
+    build.build()
+    peak = measured_peaks().get("bf16_tflops") or 1800.0
+    shapes = [  # (spatial edge, cin, cout) of the U-Net's convolutions (input padded to 16 channels)
+        (128, 16, 16), (128, 32, 16), (64, 16, 32), (64, 32, 32), (64, 64, 32), (32, 32, 64), (32, 64, 64),
+        (32, 128, 64), (16, 64, 128), (16, 128, 128)]
+    rows = []
+    g = torch.Generator(device="cuda").manual_seed(0)
+    for (e, ci, co) in shapes:
+        x = torch.randn((1, e, e, e, ci), device="cuda", generator=g).to(torch.bfloat16)
+        w = (0.1 * torch.randn((co, 27, ci), device="cuda", generator=g)).to(torch.bfloat16)
+        gy = torch.randn((1, e, e, e, co), device="cuda", generator=g).to(torch.bfloat16)
+        flop = 2.0 * e ** 3 * 27 * ci * co
+        r = {"edge": e, "cin": ci, "cout": co, "gflop": flop / 1e9}
+        for name, call in (("fwd", lambda: conv.conv3d_fwd(x, w)), ("dgrad", lambda: conv.conv3d_dgrad(gy, w)),
+                           ("wgrad", lambda: conv.conv3d_wgrad(x, gy))):
+            for _ in range(2):
+                call()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(5):
+                call()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 5
+            r[name] = {"ms": ms, "tflops": flop / (ms / 1e3) / 1e12, "frac_of_bf16_peak": flop / (ms / 1e3) / 1e12 / peak}
+        rows.append(r)
+    assert int(conv.err_word("cuda").item()) == 0
+    print(json.dumps({"mode": "convs", "bf16_peak_tflops": peak, "peak_basis": "MEASURED_PEAKS.json bf16_tflops (burst)",
+                      "note": "wgrad times include the channels-first copies of its operands", "layers": rows}),
+          flush=True)
+
+
 def main():
     args = parse()
     if args.profile_case:
         run_profile_case(args)
+    elif args.convs:
+        run_convs(args)
     elif args.paper_geometries:
         run_paper_geometries(args)
     elif args.impl == "reference":

@@ -1,4 +1,4 @@
-"""3D U-Net that maps the normalised backprojection A^T b / A^T 1 to a CGLS warm start.
+"""3D U-Net that maps the normalised backprojection A^T b / (A^T A 1) to a CGLS warm start.
 
 Four levels with 16, 32, 64, 128 channels; two 3x3x3 convolutions (+ bias, ReLU) per level;
 2x2x2 max pooling down, nearest-neighbour x2 upsampling followed by a 3x3x3 convolution that

@@ -2,8 +2,8 @@
 
 Data: seeded random-ellipsoid phantoms on the CGLS geometry (128^3 @ 0.5 mm, 180 views /
 360 deg, 256x192 detector @ 0.8 mm), projected by the CVP projector, with Poisson noise at
-1e5 photons per pixel. Network input: the normalised backprojection A^T b / A^T 1; target:
-the phantom. Evaluation: CGLS to the 1e-3 normal-equation residual from the network's
+1e5 photons per pixel. Network input: the normalised backprojection A^T b / (A^T A 1);
+target: the phantom. Evaluation: CGLS to the 1e-3 normal-equation residual from the network's
 output x0 and from 0, on held-out seeds, in iterations and wall time (the warm start's time
 includes the backprojection of b and the network's inference).
 
@@ -34,13 +34,18 @@ def phantom(geom, seed: int, device="cuda"):
 
 
 class Problem:
-    """The operator and the normalisation A^T 1 of one geometry."""
+    """The operator of one geometry and the normalisation of its backprojection.
+
+    The network input is A^T b / (A^T A 1): a constant volume c maps to c, so the input is a
+    blurred estimate of the attenuation on the target's scale (A^T b / A^T 1 would instead be
+    an average line integral, about 50 times the attenuation here)."""
 
     def __init__(self, geom, variant="relaxed"):
         self.geom = geom
         self.A = Projector(geom, variant, "cos")
-        ones = torch.ones(geom.proj_shape, device="cuda")
-        self.norm = self.A.backproject(ones).clamp_(min=1e-6)
+        ones = torch.ones(geom.vol_shape, device="cuda")
+        self.norm = self.A.backproject(self.A.project(ones))
+        self.norm.clamp_(min=1e-6 * float(self.norm.max()))
         self.ws = self.A.cgls_workspace()
 
     def data(self, truth, seed: int):
@@ -75,7 +80,7 @@ def train(model, xs, ts, epochs: int, lr: float = 1e-3, seed: int = 0, log=None)
             loss = torch.mean((out - ts[i:i + 1]) ** 2)
             loss.backward()
             opt.step()
-            tot += float(loss)
+            tot += float(loss.detach())
         hist.append(tot / xs.shape[0])
         if log:
             log(f"epoch {ep}: mean loss {hist[-1]:.3e}")
