@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--scaling", default="cos", choices=["cos", "exact"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cgls", action="store_true")
+    ap.add_argument("--accuracy", action="store_true",
+                    help="compare both variants and scalings with 64-ray supersampled ray integration and exit")
     ap.add_argument("--convs", action="store_true",
                     help="time the warm-start U-Net's tensor-core convolutions at 128^3 and exit")
     ap.add_argument("--paper-geometries", action="store_true",
@@ -539,10 +541,47 @@ def run_convs(args):
           flush=True)
 
 
+def run_accuracy(args):
+    """Accuracy of the CVP variants against supersampled ray integration (K x K = 64 rays per
+    pixel, exact path lengths; equal weights for the cos scaling, solid-angle weights for the
+    exact scaling), on 8 evenly spaced views of the 512^3 workloads (7 deg and 20 deg half
+    cone angle). Errors: |b - ref|_2 / |ref|_2 and max |b - ref| / max |ref| per workload."""
+    import torch
+
+    from paper_2110_09841_b300 import build, inputs
+    from paper_2110_09841_b300.kct import Projector
+
+    build.build()
+    out = {"mode": "accuracy", "reference": "K x K = 8 x 8 rays per pixel, exact path lengths", "results": {}}
+    for name in ("cvp512", "cvp512wide"):
+        g = inputs.workload_geometry(name)
+        g = g.subset_views(list(range(0, g.nviews, g.nviews // 8))[:8])
+        x = inputs.workload_phantom(name, device="cuda")
+        ref = {False: None, True: None}
+        res = {}
+        for weighted in (False, True):
+            ref[weighted] = Projector(g, "exact", "cos").siddon(x, K=8, weighted=weighted)
+        one = Projector(g, "exact", "cos").siddon(x, K=1)
+
+        def err(b, r):
+            return {"rel_l2": float((b - r).norm() / r.norm()), "rel_max": float((b - r).abs().max() / r.abs().max())}
+
+        res["single_ray"] = err(one, ref[False])
+        for v in ("exact", "relaxed"):
+            for sc in ("cos", "exact"):
+                b = Projector(g, v, sc).project(x)
+                res[f"{v}/{sc}"] = err(b, ref[sc == "exact"])
+        torch.cuda.synchronize()
+        out["results"][name] = res
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.profile_case:
         run_profile_case(args)
+    elif args.accuracy:
+        run_accuracy(args)
     elif args.convs:
         run_convs(args)
     elif args.paper_geometries:

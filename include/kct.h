@@ -131,8 +131,9 @@ kct_status kct_backproject(const kct_plan *plan, const float *d_proj, float *d_v
 /*
  * Batched forward projection: nbatch volumes, contiguous [nbatch][nz][ny][nx], through the
  * plan's views into nbatch projection stacks [nbatch][nviews][nv][nu], in one launch.
- * Same semantics as kct_project per batch member; ceil(nviews / 16) * nbatch must not
- * exceed 65535 (KCT_ERR_UNSUPPORTED otherwise).
+ * Same semantics as kct_project per batch member; ceil(nviews / chunk) * nbatch must not
+ * exceed 65535, chunk being the plan's views per forward block (KCT_ERR_UNSUPPORTED
+ * otherwise).
  */
 kct_status kct_project_batch(const kct_plan *plan, const float *d_vol, int32_t nbatch, float *d_proj,
                              int32_t accumulate, void *stream);
@@ -166,6 +167,18 @@ kct_status kct_plan_autotune(kct_plan *plan, const float *d_vol, float *d_proj, 
                              void *stream);
 kct_status kct_plan_set_view_chunk(kct_plan *plan, int32_t chunk);
 kct_status kct_plan_get_view_chunk(const kct_plan *plan, int32_t *chunk);
+
+/*
+ * Ray-driven comparator (not the CVP operator): for every pixel of every view, the average
+ * over K x K rays through the sub-pixel points (u - 1/2 + (a + 1/2)/K, v - 1/2 + (b + 1/2)/K)
+ * of the line integral of the volume, with exact path lengths through the voxel grid
+ * (Siddon's method; the paper's multi-ray comparison projectors, Sec. IV). weighting 0
+ * averages with equal weights (pixel-area average), 1 with the rays' solid-angle weights.
+ *   d_vol   device float32 [nz][ny][nx];  d_proj  device float32 [nviews][nv][nu], overwritten.
+ *   K in [1, 64]. Enqueued on `stream`. Used by the accuracy study of the two variants.
+ */
+kct_status kct_siddon_project(const kct_plan *plan, const float *d_vol, float *d_proj, int32_t K, int32_t weighting,
+                              void *stream);
 
 /*
  * Pixel factors F(u, v) of every view of the plan (its scaling mode) into

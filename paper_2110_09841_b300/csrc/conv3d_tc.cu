@@ -14,9 +14,10 @@
 //
 // Weight gradient (kct_conv3d_wgrad): dW[co][t][ci] = sum_v g[v][co] x[v + t][ci], a GEMM
 // with K = voxels. Operands are channels-first copies (g^T [co][v], and x^T shifted along x
-// by -1, 0, +1) so that both tiles are K-major; M = 128 rows of cout (rows >= cout are
-// zero-filled by TMA), N = cin, one TMEM accumulator per tap of the CTA's tap group, and the
-// CTA's voxel range is reduced into dW with float atomics.
+// by -1, 0, +1) so that both tiles are K-major. Taps are stacked along M: one A tile holds
+// 128 / cin taps of x (cin rows each), B is the g^T tile (N = cout), so one MMA yields dW^T
+// for several taps; a block keeps a few tap groups in TMEM, loads each g^T tile once for all
+// of them, and its voxel range is reduced into dW with float atomics.
 //
 // Every wait on an mbarrier is bounded: on timeout the kernel sets an error word, waits
 // (bounded) for its own copies in flight, frees its tensor memory and returns.
@@ -319,44 +320,54 @@ struct WgradDims {
     int kb;                              // voxels of one K chunk (a row segment along x)
     int chunks_x;                        // w / kb
     long long nchunks;                   // n * d * h * chunks_x
-    int taps_per_cta;                    // taps of one tap group
-    int tap_groups;
-    int splits;                          // voxel splits (gridDim.x = tap_groups * splits)
+    int tap_sets;                        // blocks along the taps (each takes up to GMAX tap groups)
+    int splits;                          // voxel splits (gridDim.x = tap_sets * splits)
 };
 
-template <int KB, int CI>
+constexpr int kWgStages = 2;
+
+constexpr int cmin(int a, int b) { return a < b ? a : b; }
+constexpr int pow2_at_least(int v) { return v <= 32 ? 32 : v <= 64 ? 64 : v <= 128 ? 128 : v <= 256 ? 256 : 512; }
+
+// Taps are stacked along M: an A tile holds P = 128 / CI taps of x (CI rows each), so one MMA
+// gives dW^T for P taps at once (M = 128 rows of (tap, ci), N = CO columns of cout).
+template <int KB, int CI, int CO>
 struct WgCfg {
-    static constexpr int A_BYTES = 128 * KB * 2;     // 128 rows of cout (zero-filled beyond cout)
-    static constexpr int B_BYTES = CI * KB * 2;
-    static constexpr int STAGE = ((A_BYTES + B_BYTES) + 1023) / 1024 * 1024;
-    static constexpr int TAPS = (512 / CI) < 27 ? (512 / CI) : 27;
-    static constexpr int TMEM_COLS = 512;
-    static constexpr int SMEM = 1024 + kStages * STAGE + 1024;
+    static constexpr int P = 128 / CI;                         // taps per A tile
+    static constexpr int GROUPS = (27 + P - 1) / P;            // tap groups in all
+    static constexpr int A_BYTES = 128 * KB * 2;
+    static constexpr int B_BYTES = CO * KB * 2;
+    static constexpr int GMAX = cmin(cmin(GROUPS, 512 / CO), (96 * 1024 - B_BYTES) / A_BYTES);   // groups per block
+    static constexpr int STAGE = ((GMAX * A_BYTES + B_BYTES) + 1023) / 1024 * 1024;
+    static constexpr int TMEM_COLS = pow2_at_least(GMAX * CO);
+    static constexpr int SMEM = 1024 + kWgStages * STAGE + 1024;
 };
 
-template <int KB, int CI>
+template <int KB, int CI, int CO>
 __global__ void __launch_bounds__(kThreads, 1) conv_wgrad_kernel(const __grid_constant__ CUtensorMap tm_g,
                                                                  const __grid_constant__ CUtensorMap tm_x0,
                                                                  const __grid_constant__ CUtensorMap tm_x1,
                                                                  const __grid_constant__ CUtensorMap tm_x2, WgradDims D,
                                                                  float* __restrict__ gw, int* err) {
-    using C = WgCfg<KB, CI>;
+    using C = WgCfg<KB, CI, CO>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = (uint64_t*)(smem + kStages * C::STAGE);
-    uint64_t* empty = full + kStages;
-    uint64_t* acc_full = empty + kStages;
+    uint64_t* full = (uint64_t*)(smem + kWgStages * C::STAGE);
+    uint64_t* empty = full + kWgStages;
+    uint64_t* acc_full = empty + kWgStages;
     uint32_t* tmem_slot = (uint32_t*)(acc_full + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int group = blockIdx.x % D.tap_groups, split = blockIdx.x / D.tap_groups;
-    const int tap0 = group * C::TAPS;
-    const int ntap = min(C::TAPS, 27 - tap0);
+    const int set = blockIdx.x % D.tap_sets, split = blockIdx.x / D.tap_sets;
+    const int g0 = set * C::GMAX;                              // first tap group of this block
+    const int ng = min(C::GMAX, C::GROUPS - g0);
+    const int tap0 = g0 * C::P;
+    const int ntap = min(ng * C::P, 27 - tap0);                // taps of this block
     const long long c_begin = D.nchunks * split / D.splits, c_end = D.nchunks * (split + 1) / D.splits;
-    const long long iters = (c_end - c_begin) * ntap;
+    const long long iters = c_end - c_begin;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < kWgStages; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -373,72 +384,80 @@ __global__ void __launch_bounds__(kThreads, 1) conv_wgrad_kernel(const __grid_co
         if (lane == 0) {
             long long issued = 0;
             bool ok = true;
+            const uint32_t bytes = C::B_BYTES + (uint32_t)ntap * CI * KB * 2;
             for (long long it = 0; it < iters; ++it) {
-                const int s = (int)(it % kStages);
-                const uint32_t ph = (uint32_t)(it / kStages) & 1u;
+                const int s = (int)(it % kWgStages);
+                const uint32_t ph = (uint32_t)(it / kWgStages) & 1u;
                 if (!mbar_wait(&empty[s], ph ^ 1u)) { ok = false; break; }
-                long long c = c_begin + it / ntap;
-                const int j = (int)(it % ntap), tap = tap0 + j;
-                const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+                long long c = c_begin + it;
                 const int cx = (int)(c % D.chunks_x);
                 c /= D.chunks_x;
                 const int yv = (int)(c % D.h);
                 c /= D.h;
                 const int zv = (int)(c % D.d);
                 const int nb = (int)(c / D.d);
-                uint8_t* a = smem + s * C::STAGE;
-                uint8_t* b = a + C::A_BYTES;
-                mbar_expect_tx(&full[s], C::A_BYTES + C::B_BYTES);
-                // g^T [n][co][z][y][x]: dims (x, y, z, co, n)
-                tma_load_5d(a, &tm_g, cx * KB, yv, zv, 0, nb, &full[s]);
-                const CUtensorMap* tx = dx == 0 ? &tm_x0 : dx == 1 ? &tm_x1 : &tm_x2;
-                tma_load_5d(b, tx, cx * KB, yv + dy - 1, zv + dz - 1, 0, nb, &full[s]);
+                uint8_t* b = smem + s * C::STAGE;
+                uint8_t* a = b + C::B_BYTES;
+                mbar_expect_tx(&full[s], bytes);
+                // g^T [n][co][z][y][x]: dims (x, y, z, co, n), CO rows
+                tma_load_5d(b, &tm_g, cx * KB, yv, zv, 0, nb, &full[s]);
+                for (int j = 0; j < ntap; ++j) {
+                    const int tap = tap0 + j;
+                    const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+                    const CUtensorMap* tx = dx == 0 ? &tm_x0 : dx == 1 ? &tm_x1 : &tm_x2;
+                    uint8_t* dst = a + (j / C::P) * C::A_BYTES + (j % C::P) * CI * KB * 2;
+                    tma_load_5d(dst, tx, cx * KB, yv + dy - 1, zv + dz - 1, 0, nb, &full[s]);
+                }
                 ++issued;
             }
             if (!ok) {
                 atomicExch(err, 1);
-                for (long long it = issued - kStages < 0 ? 0 : issued - kStages; it < issued; ++it)
-                    mbar_wait(&full[it % kStages], (uint32_t)(it / kStages) & 1u);
+                for (long long it = issued - kWgStages < 0 ? 0 : issued - kWgStages; it < issued; ++it)
+                    mbar_wait(&full[it % kWgStages], (uint32_t)(it / kWgStages) & 1u);
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16(128, CI);
+            const uint32_t idesc = idesc_bf16(128, CO);
             bool ok = true;
             for (long long it = 0; it < iters; ++it) {
-                const int s = (int)(it % kStages);
-                const uint32_t ph = (uint32_t)(it / kStages) & 1u;
+                const int s = (int)(it % kWgStages);
+                const uint32_t ph = (uint32_t)(it / kWgStages) & 1u;
                 if (!mbar_wait(&full[s], ph)) { ok = false; break; }
                 tc_fence_after();
-                const int j = (int)(it % ntap);
-                const bool first_chunk = it < ntap;
-                const uint32_t a = smem_u32(smem + s * C::STAGE);
-                const uint32_t b = a + C::A_BYTES;
+                const uint32_t b = smem_u32(smem + s * C::STAGE);
+                const uint32_t a = b + C::B_BYTES;
+                for (int g = 0; g < ng; ++g) {
 #pragma unroll
-                for (int k = 0; k < KB / 16; ++k)
-                    umma_bf16(tmem + (uint32_t)(j * CI), kmajor_desc(a + 32 * k, KB * 2), kmajor_desc(b + 32 * k, KB * 2),
-                              idesc, (!first_chunk || k > 0) ? 1u : 0u);
+                    for (int k = 0; k < KB / 16; ++k)
+                        umma_bf16(tmem + (uint32_t)(g * CO), kmajor_desc(a + g * C::A_BYTES + 32 * k, KB * 2),
+                                  kmajor_desc(b + 32 * k, KB * 2), idesc, (it > 0 || k > 0) ? 1u : 0u);
+                }
                 umma_commit(&empty[s]);
             }
             if (!ok) atomicExch(err, 1);
             umma_commit(acc_full);
         }
     } else {
-        const int row = 32 * (warp & 3) + lane;      // cout index
+        // TMEM lane r of group g holds tap tap0 + g * P + r / CI, input channel r % CI
+        const int row = 32 * (warp & 3) + lane;
         const bool ok = mbar_wait(acc_full, 0);
         tc_fence_after();
         if (!ok) {
             if (lane == 0) atomicExch(err, 1);
         } else if (iters > 0) {
-            for (int j = 0; j < ntap; ++j) {
+            for (int g = 0; g < ng; ++g) {
+                const int j = g * C::P + row / CI;
+                const bool valid = row / CI < C::P && j < ntap;
+                const int ci = row % CI;
 #pragma unroll
-                for (int c0 = 0; c0 < CI; c0 += 16) {
+                for (int c0 = 0; c0 < CO; c0 += 16) {
                     float v[16];
-                    tmem_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(j * CI + c0), v);
-                    if (row < D.cout) {
-                        float* dst = gw + ((size_t)row * 27 + (tap0 + j)) * D.cin + c0;
+                    tmem_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(g * CO + c0), v);
+                    if (valid) {
 #pragma unroll
-                        for (int q = 0; q < 16; ++q) atomicAdd(dst + q, v[q]);
+                        for (int q = 0; q < 16; ++q)
+                            if (c0 + q < D.cout) atomicAdd(gw + ((size_t)(c0 + q) * 27 + (tap0 + j)) * D.cin + ci, v[q]);
                     }
                 }
             }
@@ -538,36 +557,49 @@ int dispatch_fwd_cout(const CUtensorMap& tx, const CUtensorMap& tw, const ConvDi
     return conv_fail(KCT_ERR_UNSUPPORTED, "cout must be 16, 32, 48, 64, 96 or 128");
 }
 
-template <int KB, int CI>
+template <int KB, int CI, int CO>
 int launch_wgrad(const CUtensorMap& tg, const CUtensorMap* tx, WgradDims D, float* gw, int* err, int sms,
                  cudaStream_t st) {
-    using C = WgCfg<KB, CI>;
-    D.taps_per_cta = C::TAPS;
-    D.tap_groups = (27 + C::TAPS - 1) / C::TAPS;
-    long long splits = (2LL * sms + D.tap_groups - 1) / D.tap_groups;
+    using C = WgCfg<KB, CI, CO>;
+    D.tap_sets = (C::GROUPS + C::GMAX - 1) / C::GMAX;
+    long long splits = (2LL * sms + D.tap_sets - 1) / D.tap_sets;
     if (splits > D.nchunks) splits = D.nchunks;
     if (splits < 1) splits = 1;
     D.splits = (int)splits;
     const int smem = smem_request(C::SMEM, C::TMEM_COLS);
-    cudaError_t e = allow_smem(conv_wgrad_kernel<KB, CI>, smem);
+    cudaError_t e = allow_smem(conv_wgrad_kernel<KB, CI, CO>, smem);
     if (e != cudaSuccess) return conv_fail(KCT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
-    conv_wgrad_kernel<KB, CI><<<(unsigned)(D.tap_groups * D.splits), kThreads, smem, st>>>(tg, tx[0], tx[1], tx[2], D,
-                                                                                         gw, err);
+    conv_wgrad_kernel<KB, CI, CO><<<(unsigned)(D.tap_sets * D.splits), kThreads, smem, st>>>(tg, tx[0], tx[1], tx[2],
+                                                                                           D, gw, err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return conv_fail(KCT_ERR_CUDA, std::string("conv weight-gradient launch: ") + cudaGetErrorString(e));
     return KCT_OK;
+}
+
+template <int KB, int CI>
+int dispatch_wgrad_co(const CUtensorMap& tg, const CUtensorMap* tx, const WgradDims& D, float* gw, int* err, int sms,
+                      cudaStream_t st) {
+    switch (D.cout) {
+        case 16: return launch_wgrad<KB, CI, 16>(tg, tx, D, gw, err, sms, st);
+        case 32: return launch_wgrad<KB, CI, 32>(tg, tx, D, gw, err, sms, st);
+        case 48: return launch_wgrad<KB, CI, 48>(tg, tx, D, gw, err, sms, st);
+        case 64: return launch_wgrad<KB, CI, 64>(tg, tx, D, gw, err, sms, st);
+        case 96: return launch_wgrad<KB, CI, 96>(tg, tx, D, gw, err, sms, st);
+        case 128: return launch_wgrad<KB, CI, 128>(tg, tx, D, gw, err, sms, st);
+    }
+    return conv_fail(KCT_ERR_UNSUPPORTED, "cout must be 16, 32, 48, 64, 96 or 128");
 }
 
 template <int KB>
 int dispatch_wgrad_ci(const CUtensorMap& tg, const CUtensorMap* tx, const WgradDims& D, float* gw, int* err, int sms,
                       cudaStream_t st) {
     switch (D.cin) {
-        case 16: return launch_wgrad<KB, 16>(tg, tx, D, gw, err, sms, st);
-        case 32: return launch_wgrad<KB, 32>(tg, tx, D, gw, err, sms, st);
-        case 48: return launch_wgrad<KB, 48>(tg, tx, D, gw, err, sms, st);
-        case 64: return launch_wgrad<KB, 64>(tg, tx, D, gw, err, sms, st);
-        case 96: return launch_wgrad<KB, 96>(tg, tx, D, gw, err, sms, st);
-        case 128: return launch_wgrad<KB, 128>(tg, tx, D, gw, err, sms, st);
+        case 16: return dispatch_wgrad_co<KB, 16>(tg, tx, D, gw, err, sms, st);
+        case 32: return dispatch_wgrad_co<KB, 32>(tg, tx, D, gw, err, sms, st);
+        case 48: return dispatch_wgrad_co<KB, 48>(tg, tx, D, gw, err, sms, st);
+        case 64: return dispatch_wgrad_co<KB, 64>(tg, tx, D, gw, err, sms, st);
+        case 96: return dispatch_wgrad_co<KB, 96>(tg, tx, D, gw, err, sms, st);
+        case 128: return dispatch_wgrad_co<KB, 128>(tg, tx, D, gw, err, sms, st);
     }
     return conv_fail(KCT_ERR_UNSUPPORTED, "cin must be 16, 32, 48, 64, 96 or 128");
 }
@@ -647,7 +679,7 @@ int kct_conv3d_wgrad(const kct_conv_desc* c, const void* d_gt, const void* d_xt0
         return make_map(m, p, 5, dd, ss, bb, D.kb * 2);
     };
     CUtensorMap tg, tx[3];
-    if ((s = cf_map(&tg, d_gt, c->cout, 128)) != KCT_OK) return s;
+    if ((s = cf_map(&tg, d_gt, c->cout, c->cout)) != KCT_OK) return s;
     if ((s = cf_map(&tx[0], d_xt0, c->cin, c->cin)) != KCT_OK) return s;
     if ((s = cf_map(&tx[1], d_xt1, c->cin, c->cin)) != KCT_OK) return s;
     if ((s = cf_map(&tx[2], d_xt2, c->cin, c->cin)) != KCT_OK) return s;

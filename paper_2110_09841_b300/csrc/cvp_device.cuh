@@ -57,7 +57,7 @@ struct View {
     float sq_t[4], sq_x[4];      // voxel base square vertices (t', xi'), counter-clockwise
     float tmin_sq, tmax_sq;      // t' range of the square
     float sq_tt, sq_tx;          // Green sums of the full square for t'^2 and t' xi'
-    float pad[2];
+    float sx, sy;                // source s_1, s_2 (used by the ray-driven comparator only)
 };
 
 struct Grid {

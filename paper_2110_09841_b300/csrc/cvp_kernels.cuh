@@ -46,6 +46,7 @@ struct WarpSmem {
     int nv[KCT_CB];
     float4 fa[KCT_CB];             // exact: moments of H_n m1, mt, mtt, ml; relaxed: A_n, t_n, 1/t_n, -
     float4 fb[KCT_CB];             // exact: mlt, t'-range of H_n (lo, hi), -
+    float2 fr[KCT_CB];             // exact: 1 / depth at the two ends of that range
     float ev_p0[EV_CAP], ev_p1[EV_CAP], ev_zs[EV_CAP];
     float res_v[EV_CAP], res_q[EV_CAP];
 };
@@ -153,7 +154,8 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
             // rows touched by this voxel over the depth range of H_n
             int m_first = 0, R = 0;
             if (act && fa.x > 0.f) {
-                const float i0 = 1.0f / (C.tc + tlo), i1 = 1.0f / (C.tc + thi);
+                const float2 fr = ws->fr[c];
+                const float i0 = fr.x, i1 = fr.y;
                 const float zl = zc - 0.5f * az, zh = zc + 0.5f * az;
                 const float b0 = fminf(fminf(zl * i0, zl * i1), fminf(zh * i0, zh * i1));
                 const float b1 = fmaxf(fmaxf(zl * i0, zl * i1), fmaxf(zh * i0, zh * i1));
@@ -350,6 +352,7 @@ __device__ __noinline__ void build_column_cut(const View* Vp, const Column* Cp, 
     } else {
         ws->fa[c] = make_float4(f.m1, f.mt, f.mtt, f.ml);
         ws->fb[c] = make_float4(f.mlt, tlo, thi, 0.f);
+        ws->fr[c] = make_float2(1.0f / (C.tc + tlo), 1.0f / (C.tc + thi));
     }
 }
 

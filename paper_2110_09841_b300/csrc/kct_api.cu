@@ -15,6 +15,7 @@
 #include "cvp_device.cuh"
 #include "cvp_kernels.cuh"
 #include "cgls_kernels.cuh"
+#include "siddon.cuh"
 
 using kct::Grid;
 using kct::View;
@@ -160,7 +161,8 @@ std::string setup_view(const double* P, const kct_volume_desc& vol, View& V) {
     }
     V.sq_tt = (float)stt;
     V.sq_tx = (float)stx;
-    V.pad[0] = V.pad[1] = 0.f;
+    V.sx = (float)s[0];
+    V.sy = (float)s[1];
     return std::string();
 }
 
@@ -490,6 +492,23 @@ kct_status kct_plan_autotune(kct_plan* p, const float* d_vol, float* d_proj, int
     p->fwd_chunk = best;
     if (chunk) *chunk = best;
     if (ms) *ms = best_ms;
+    return KCT_OK;
+}
+
+kct_status kct_siddon_project(const kct_plan* p, const float* d_vol, float* d_proj, int32_t K, int32_t weighting,
+                              void* stream) {
+    kct_status s = check_plan(p);
+    if (s != KCT_OK) return s;
+    if (!d_vol || !d_proj) return fail(KCT_ERR_INVALID_ARG, "null data pointer");
+    if (K < 1 || K > 64) return fail(KCT_ERR_INVALID_ARG, "K must be in [1, 64]");
+    if ((s = set_device(p)) != KCT_OK) return s;
+    const Grid& G = p->grid;
+    const long long npix = (long long)G.nu * G.nv;
+    dim3 grid((unsigned)((npix + 7) / 8), (unsigned)G.nviews);
+    if (weighting) kct::siddon_kernel<1><<<grid, 256, 0, (cudaStream_t)stream>>>(p->d_views, G, d_vol, d_proj, K);
+    else kct::siddon_kernel<0><<<grid, 256, 0, (cudaStream_t)stream>>>(p->d_views, G, d_vol, d_proj, K);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "ray-driven comparator launch");
     return KCT_OK;
 }
 

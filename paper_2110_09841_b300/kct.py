@@ -26,7 +26,7 @@ EXPORTED = ["kct_plan_create", "kct_plan_destroy", "kct_project", "kct_backproje
             "kct_pixel_factors", "kct_count_pairs", "kct_last_device_error", "kct_status_string",
             "kct_last_error_message", "kct_version", "kct_project_static", "kct_project_batch",
             "kct_backproject_batch", "kct_cgls_workspace_bytes", "kct_cgls", "kct_plan_autotune",
-            "kct_plan_set_view_chunk", "kct_plan_get_view_chunk"]
+            "kct_plan_set_view_chunk", "kct_plan_get_view_chunk", "kct_siddon_project"]
 
 
 class KctError(RuntimeError):
@@ -91,6 +91,8 @@ def load(path: str | None = None):
         lib.kct_project_static.argtypes = [ctypes.POINTER(VolumeDesc), ctypes.POINTER(DetectorDesc), V, I32, I, I,
                                            V, V, I32, V]
         lib.kct_project_static.restype = I
+        lib.kct_siddon_project.argtypes = [V, V, V, I32, I32, V]
+        lib.kct_siddon_project.restype = I
         lib.kct_plan_autotune.argtypes = [V, V, V, ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_float), V]
         lib.kct_plan_autotune.restype = I
         lib.kct_plan_set_view_chunk.argtypes = [V, I32]
@@ -282,6 +284,18 @@ class Projector:
         k = int(rep.iterations)
         return out, dict(iterations=k, converged=bool(rep.converged), normal=hn[:k + 1].copy(),
                          data=hd[:k + 1].copy())
+
+    def siddon(self, x, K=8, weighted=False, out=None, stream=None):
+        """Ray-driven comparator: K x K rays per pixel, exact path lengths (kct_siddon_project)."""
+        import torch
+
+        g = self.geom
+        xp = _dev_ptr(x, g.vol_shape, "x")
+        if out is None:
+            out = torch.empty(g.proj_shape, dtype=torch.float32, device=x.device)
+        _check(self.lib.kct_siddon_project(self._h, xp, _dev_ptr(out, g.proj_shape, "out"), int(K), int(bool(weighted)),
+                                           _stream_handle(stream)))
+        return out
 
     def pixel_factors(self, stream=None):
         import torch
