@@ -24,12 +24,13 @@ def _c(p, name, x, relu=True):
     return torch.relu(y) if relu else y
 
 
-def forward(p: dict, inp: torch.Tensor, levels: int = 4, base: int = 16) -> torch.Tensor:
+def forward(p: dict, inp: torch.Tensor, levels: int = 4, base: int = 16, scale: float = 1.0) -> torch.Tensor:
     """p: float64 parameters by name ([cout, 27, cin] weights, [cout] biases);
-    inp: float64 [n, d, h, w] -> float64 [n, d, h, w]."""
+    inp: float64 [n, d, h, w] -> float64 [n, d, h, w]. The network sees inp * scale and its
+    correction is divided by scale."""
     n, d, h, w = inp.shape
     x = torch.zeros((n, base, d, h, w), dtype=torch.float64)
-    x[:, 0] = inp
+    x[:, 0] = inp * scale
     skips = []
     for i in range(levels):
         if i > 0:
@@ -44,4 +45,4 @@ def forward(p: dict, inp: torch.Tensor, levels: int = 4, base: int = 16) -> torc
         x = _c(p, f"dec{i}a", x)
         x = _c(p, f"dec{i}b", x)
     y = _c(p, "head", x, relu=False)
-    return inp + y[:, 0]
+    return inp + y[:, 0] / scale

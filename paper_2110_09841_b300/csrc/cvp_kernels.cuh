@@ -234,10 +234,15 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
                         const Mom full_m = Mom{fa.x, fa.y, fa.z, fa.w, fb.x};
                         const float tau0 = -p0 / p1s, tau1 = (az - p0) / p1s;
                         const Mom zero_m = Mom{0.f, 0.f, 0.f, 0.f, 0.f};
-                        const Mom c0 = (tau0 <= tlo) ? zero_m : (tau0 >= thi) ? full_m
-                                       : cut_moments_call(ws->pt[c], ws->px[c], ws->nv[c], tau0, C.tc, C.xc);
-                        const Mom c1 = (tau1 <= tlo) ? zero_m : (tau1 >= thi) ? full_m
-                                       : cut_moments_call(ws->pt[c], ws->px[c], ws->nv[c], tau1, C.tc, C.xc);
+                        // A plane usually leaves through one face only, so one of the two depths
+                        // lies inside H_n's depth range: one call site serves every lane (a
+                        // second one only for planes that cross both faces within H_n).
+                        const bool in0 = tau0 > tlo && tau0 < thi, in1 = tau1 > tlo && tau1 < thi;
+                        Mom ca = zero_m, cb = zero_m;
+                        if (in0 || in1) ca = cut_moments_call(ws->pt[c], ws->px[c], ws->nv[c], in0 ? tau0 : tau1, C.tc, C.xc);
+                        if (in0 && in1) cb = cut_moments_call(ws->pt[c], ws->px[c], ws->nv[c], tau1, C.tc, C.xc);
+                        const Mom c0 = in0 ? ca : (tau0 <= tlo) ? zero_m : full_m;
+                        const Mom c1 = in1 ? (in0 ? cb : ca) : (tau1 <= tlo) ? zero_m : full_m;
                         float gv, gq;
                         g_cross_from(az, c0, c1, full_m, p0, p1, p1s, ws->ev_zs[e], gv, gq);
                         ws->res_v[e] = gv;
@@ -270,14 +275,14 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
                                 float p0 = fmaf(0.5f, az, fmaf((float)b, dp0, off0)), p1 = fmaf((float)b, dp1, p1_0);
                                 if (zero & bit) { p0 = 0.f; p1 = 0.f; }
                                 if (full & bit) { p0 = az; p1 = 0.f; }
+                                // the linear form in the row's frame is evaluated by every lane (no
+                                // divergence on the frame); crossing planes then take the queued result
+                                g_lin(az, top ? az - p0 : p0, top ? -p1 : p1, top ? -zs : zs, fa.x, fa.y, fa.z, fa.w, fb.x,
+                                      g[h][0], g[h][1]);
                                 if (cross & bit) {
                                     const int q = top ? e0 + nbot + __popc(mtop & (bit - 1u)) : e0 + __popc(mbot & (bit - 1u));
                                     g[h][0] = ws->res_v[q];
                                     g[h][1] = ws->res_q[q];
-                                } else if (top) {
-                                    g_lin(az, az - p0, -p1, -zs, fa.x, fa.y, fa.z, fa.w, fb.x, g[h][0], g[h][1]);
-                                } else {
-                                    g_lin(az, p0, p1, zs, fa.x, fa.y, fa.z, fa.w, fb.x, g[h][0], g[h][1]);
                                 }
                             }
                             pv = top ? g[0][0] - g[1][0] : g[1][0] - g[0][0];

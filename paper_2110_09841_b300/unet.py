@@ -4,7 +4,8 @@ Four levels with 16, 32, 64, 128 channels; two 3x3x3 convolutions (+ bias, ReLU)
 2x2x2 max pooling down, nearest-neighbour x2 upsampling followed by a 3x3x3 convolution that
 halves the channels up, concatenation with the skip connection, two convolutions; a final
 3x3x3 convolution whose channel 0 is added to the input (the network learns a correction of
-the normalised backprojection). Activations are channels-last bf16 [n, d, h, w, c]; every
+the normalised backprojection). Inside the network the input and the correction are
+multiplied by a fixed scale (set from the training targets) so that activations are O(1). Activations are channels-last bf16 [n, d, h, w, c]; every
 convolution (forward and both gradients) runs in the tensor-core kernels of libkct_conv;
 pooling, upsampling, concatenation and the loss are torch glue.
 
@@ -53,6 +54,9 @@ class UNet3D(torch.nn.Module):
         add("head", base, base)
         with torch.no_grad():                            # start as the identity correction
             self.head_w.zero_()
+        # inputs and corrections are scaled by this factor inside the network, so that its
+        # activations are O(1) whatever the attenuation scale of the data
+        self.register_buffer("scale", torch.ones(()))
 
     def _c(self, name, x, relu=True):
         return conv.conv3d(x, getattr(self, name + "_w"), getattr(self, name + "_b"), relu)
@@ -70,7 +74,7 @@ class UNet3D(torch.nn.Module):
         """inp: float [n, d, h, w] (normalised backprojection) -> float [n, d, h, w]."""
         n, d, h, w = inp.shape
         x = torch.zeros((n, d, h, w, self.ch[0]), dtype=torch.bfloat16, device=inp.device)
-        x[..., 0] = inp.to(torch.bfloat16)
+        x[..., 0] = (inp * self.scale).to(torch.bfloat16)
         skips = []
         for i in range(self.levels):
             if i > 0:
@@ -84,4 +88,4 @@ class UNet3D(torch.nn.Module):
             x = self._c(f"dec{i}a", x)
             x = self._c(f"dec{i}b", x)
         y = self._c("head", x, relu=False)
-        return inp + y[..., 0].float()
+        return inp + y[..., 0].float() / self.scale

@@ -13,6 +13,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import time
 
 import torch
@@ -55,20 +56,33 @@ class Problem:
         return self.A.backproject(b) / self.norm
 
 
-def generate(prob: Problem, seeds):
-    """(inputs, targets) float32 [N, nz, ny, nx] on the GPU."""
+def generate(prob: Problem, seeds, target="phantom", tol=1e-3, max_iter=300):
+    """(inputs, targets) float32 [N, nz, ny, nx] on the GPU. target "phantom": the phantom;
+    "cgls": the CGLS solution from 0 at the stopping tolerance (what the warm start should
+    reproduce so that few steps remain)."""
     g = prob.geom
     xs = torch.empty((len(seeds),) + g.vol_shape, device="cuda")
     ts = torch.empty_like(xs)
     for i, s in enumerate(seeds):
         t = phantom(g, s)
-        ts[i] = t
-        xs[i] = prob.network_input(prob.data(t, s))
+        b = prob.data(t, s)
+        xs[i] = prob.network_input(b)
+        if target == "cgls":
+            prob.A.cgls(b, max_iter=max_iter, tol=tol, out=ts[i], workspace=prob.ws)
+        else:
+            ts[i] = t
     return xs, ts
 
 
 def train(model, xs, ts, epochs: int, lr: float = 1e-3, seed: int = 0, log=None):
+    """Adam on the mean squared error, one volume per step, learning rate decaying along a
+    cosine from lr to lr / 20; the network's internal scale is set to 1 / mean |target|."""
+    with torch.no_grad():
+        model.scale.fill_(1.0 / float(ts.abs().mean().clamp(min=1e-12)))
     opt = torch.optim.Adam(model.parameters(), lr=lr)
+    steps = max(1, epochs * xs.shape[0])
+    sched = torch.optim.lr_scheduler.LambdaLR(
+        opt, lambda k: 0.05 + 0.95 * 0.5 * (1.0 + math.cos(math.pi * min(k, steps) / steps)))
     gen = torch.Generator().manual_seed(seed)
     hist = []
     for ep in range(epochs):
@@ -80,6 +94,7 @@ def train(model, xs, ts, epochs: int, lr: float = 1e-3, seed: int = 0, log=None)
             loss = torch.mean((out - ts[i:i + 1]) ** 2)
             loss.backward()
             opt.step()
+            sched.step()
             tot += float(loss.detach())
         hist.append(tot / xs.shape[0])
         if log:
@@ -135,6 +150,7 @@ def main():
     ap.add_argument("--eval", type=int, default=100)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--variant", default="relaxed", choices=["exact", "relaxed"])
+    ap.add_argument("--target", default="phantom", choices=["phantom", "cgls"])
     ap.add_argument("--out", default=None)
     args = ap.parse_args()
     from . import build
@@ -143,7 +159,7 @@ def main():
     g = inputs.workload_geometry("cgls128")
     prob = Problem(g, args.variant)
     t0 = time.perf_counter()
-    xs, ts = generate(prob, range(TRAIN_SEED0, TRAIN_SEED0 + args.train))
+    xs, ts = generate(prob, range(TRAIN_SEED0, TRAIN_SEED0 + args.train), args.target)
     t_data = time.perf_counter() - t0
     model = UNet3D().cuda()
     t0 = time.perf_counter()
@@ -152,7 +168,8 @@ def main():
     t_train = time.perf_counter() - t0
     del xs, ts
     rows = evaluate(model, prob, range(EVAL_SEED0, EVAL_SEED0 + args.eval))
-    out = {"workload": "cgls128", "variant": args.variant, "train_samples": args.train, "epochs": args.epochs,
+    out = {"workload": "cgls128", "variant": args.variant, "target": args.target, "train_samples": args.train,
+           "epochs": args.epochs, "lr": args.lr,
            "data_s": t_data, "train_s": t_train, "loss": hist, "summary": summarise(rows), "per_seed": rows}
     print(json.dumps(out["summary"]))
     if args.out:

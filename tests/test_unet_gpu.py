@@ -26,6 +26,7 @@ def cos(a, b):
 
 def test_forward_and_gradients_match_oracle():
     model = UNet3D(seed=3).cuda()
+    model.scale.fill_(4.0)
     with torch.no_grad():                          # give the head nonzero weights so every layer gets gradient
         model.head_w.normal_(0.0, 0.05, generator=torch.Generator(device="cuda").manual_seed(1))
     g = torch.Generator().manual_seed(7)
@@ -37,10 +38,11 @@ def test_forward_and_gradients_match_oracle():
 
     # the oracle gets the bf16-rounded weights the GPU network used
     p = {name: t.detach().cpu().double() for name, t in model.named_parameters()}
+    scale = float(model.scale)
     for n in model.names:
         p[n + "_w"] = model.get_parameter(n + "_w").detach().to(torch.bfloat16).cpu().double().requires_grad_(True)
         p[n + "_b"] = p[n + "_b"].requires_grad_(True)
-    ref = ounet.forward(p, inp.double())
+    ref = ounet.forward(p, inp.double(), scale=scale)
     rloss = torch.mean((ref - target.double()) ** 2)
     rloss.backward()
     assert rel(out.detach().cpu().double(), ref.detach()) < 3e-2
