@@ -18,10 +18,10 @@ def lib():
     return kct.load()
 
 
-def declared_functions():
-    src = open(os.path.join(ROOT, "include", "kct.h")).read()
+def declared_functions(header="kct.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(kct_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(kct_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_exports_every_declared_symbol(lib):
@@ -29,6 +29,23 @@ def test_exports_every_declared_symbol(lib):
     assert set(names) == set(kct.EXPORTED)
     for n in names:
         assert hasattr(lib, n), n
+
+
+def test_conv_library_exports_every_declared_symbol():
+    from paper_2110_09841_b300 import conv
+
+    build.build()
+    clib = conv.load()
+    names = declared_functions("kct_conv.h")
+    assert set(names) == {"kct_conv3d_fwd", "kct_conv3d_wgrad", "kct_conv_last_error"}
+    for n in names:
+        assert hasattr(clib, n), n
+    # invalid descriptors are rejected before any launch
+    d = conv.ConvDesc(1, 4, 8, 16, 24, 16)               # cin not a multiple of 16
+    assert clib.kct_conv3d_fwd(ctypes.byref(d), None, None, None, None, 0, None, None) == 6
+    d = conv.ConvDesc(1, 4, 8, 16, 16, 16)
+    assert clib.kct_conv3d_fwd(ctypes.byref(d), None, None, None, None, 0, None, None) == 1
+    assert clib.kct_conv3d_fwd(None, None, None, None, None, 0, None, None) == 1
 
 
 def test_version_and_status_strings(lib):
