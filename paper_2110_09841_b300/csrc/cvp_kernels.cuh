@@ -32,7 +32,7 @@ constexpr int BX = 8, BY = 8;      // voxel columns of a brick
 constexpr int NCOLS = BX * BY;
 constexpr int NWARP = 8;           // warps per block
 constexpr int NTHREADS = 32 * NWARP;
-constexpr int EV_CAP = 64;         // crossing events queued per warp and round
+constexpr int EV_CAP = 64;         // crossing events queued per warp and round (>= KPL * KCT_ROWS)
 constexpr int KCT_ROWS = 32;       // row boundaries of one voxel (its footprint spans <= 31 rows)
 constexpr int TILE_CAP = 8192;     // floats of the shared detector tile
 constexpr int VIEW_CHUNK = 16;     // default views per forward block (a plan may tune it)
@@ -139,126 +139,162 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
     const float az = G.az;
     const float dp0 = C.tc * V.inv_agv, dp1 = V.inv_agv;   // change of p0, p1 from one row boundary to the next
     const float vtiny = 1e-9f * G.ax * G.ay * az;
-    for (int pass = 0; pass < KPL; ++pass) {
-        const int k = kbase + pass * 32 + lane;
-        const bool act = k < G.nz;
-        const float zc = fmaf((float)k, az, G.z0) - V.sz;     // zeta of the voxel centre
-        const float bc = zc * C.itc;
-        const float zs = zc * V.sgv;
-        const float D2 = fmaf(C.tc, C.tc, fmaf(C.xc, C.xc, zc * zc));
-        if (act) sink.begin(pass, k);
+    // the lane's voxels kbase + lane + 32 p; their crossing planes share one queue round
+#pragma unroll
+    for (int p = 0; p < KPL; ++p) {
+        const int k = kbase + p * 32 + lane;
+        if (k < G.nz) sink.begin(p, k);
+    }
 #pragma unroll 1
-        for (int c = 0; c < ncol; ++c) {
-            const float4 fa = ws->fa[c], fb = ws->fb[c];
-            const float tlo = fb.y, thi = fb.z;
+    for (int c = 0; c < ncol; ++c) {
+        const float4 fa = ws->fa[c], fb = ws->fb[c];
+        const float tlo = fb.y, thi = fb.z;
+        const float2 fr = ws->fr[c];
+        int m_first[KPL], R[KPL];
+        unsigned cross[KPL], zero[KPL], full[KPL];
+        int nev[KPL];
+#pragma unroll
+        for (int p = 0; p < KPL; ++p) {
+            const int k = kbase + p * 32 + lane;
+            const float zc = fmaf((float)k, az, G.z0) - V.sz;     // zeta of the voxel centre
             // rows touched by this voxel over the depth range of H_n
-            int m_first = 0, R = 0;
-            if (act && fa.x > 0.f) {
-                const float2 fr = ws->fr[c];
-                const float i0 = fr.x, i1 = fr.y;
+            m_first[p] = 0;
+            R[p] = 0;
+            if (k < G.nz && fa.x > 0.f) {
                 const float zl = zc - 0.5f * az, zh = zc + 0.5f * az;
-                const float b0 = fminf(fminf(zl * i0, zl * i1), fminf(zh * i0, zh * i1));
-                const float b1 = fmaxf(fmaxf(zl * i0, zl * i1), fmaxf(zh * i0, zh * i1));
+                const float b0 = fminf(fminf(zl * fr.x, zl * fr.y), fminf(zh * fr.x, zh * fr.y));
+                const float b1 = fmaxf(fmaxf(zl * fr.x, zl * fr.y), fmaxf(zh * fr.x, zh * fr.y));
                 const float va = fmaf(V.gv, b0, V.cv), vb = fmaf(V.gv, b1, V.cv);
-                m_first = max((int)floorf(fminf(va, vb) + 0.5f), 0);
+                m_first[p] = max((int)floorf(fminf(va, vb) + 0.5f), 0);
                 const int m_last = min((int)floorf(fmaxf(va, vb) + 0.5f), G.nv - 1);
-                R = m_last - m_first + 1;
-                if (R + 1 > KCT_ROWS) { atomicOr(err, 1); R = 0; }
-                if (R < 0) R = 0;
+                R[p] = m_last - m_first[p] + 1;
+                if (R[p] + 1 > KCT_ROWS) { atomicOr(err, 1); R[p] = 0; }
+                if (R[p] < 0) R[p] = 0;
             }
-            const int rb = (R + 1) >> 1;                        // rows r < rb use the bottom frame
             // height of {v < V_b} over t' is p0 + p1 t', p0 = az/2 + tc (V_b - v_c)/|gv|, p1 = (V_b - cv)/|gv|
-            const float off0 = C.tc * (-fmaf(V.gv, bc, V.cv - ((float)m_first - 0.5f))) * V.inv_agv;
-            const float p1_0 = ((float)m_first - 0.5f - V.cv) * V.inv_agv;
+            const float off0 = C.tc * (-fmaf(V.gv, zc * C.itc, V.cv - ((float)m_first[p] - 0.5f))) * V.inv_agv;
+            const float p1_0 = ((float)m_first[p] - 0.5f - V.cv) * V.inv_agv;
             // classes of the boundaries: 0 / az for planes outside the voxel, crossing mask
-            unsigned cross = 0u, zero = 0u, full = 0u;
+            unsigned cr = 0u, ze = 0u, fu = 0u;
 #pragma unroll 1
-            for (int b = 0; b <= R; ++b) {
+            for (int b = 0; b <= R[p]; ++b) {
                 const float p0 = fmaf(0.5f, az, fmaf((float)b, dp0, off0)), p1 = fmaf((float)b, dp1, p1_0);
                 const float h0 = fmaf(p1, tlo, p0), h1 = fmaf(p1, thi, p0);
                 const float hmin = fminf(h0, h1), hmax = fmaxf(h0, h1);
-                if (hmax <= 0.f) zero |= 1u << b;
-                else if (hmin >= az) full |= 1u << b;
-                else if (hmin < 0.f || hmax > az) cross |= 1u << b;
+                if (hmax <= 0.f) ze |= 1u << b;
+                else if (hmin >= az) fu |= 1u << b;
+                else if (hmin < 0.f || hmax > az) cr |= 1u << b;
             }
-            const unsigned mbot = cross & ((2u << rb) - 1u);
-            const unsigned mtop = cross & ~((1u << rb) - 1u);
-            const int nbot = __popc(mbot);
-            const int nev = nbot + __popc(mtop);
-            int base = 0, total = 0;
-            if (__any_sync(FULLMASK, nev > 0)) {
-                int incl = nev;
+            cross[p] = cr;
+            zero[p] = ze;
+            full[p] = fu;
+            const int rb = (R[p] + 1) >> 1;                     // rows r < rb use the bottom frame
+            // planes b <= rb give a bottom-frame event, b >= rb a top-frame one
+            nev[p] = __popc(cr & ((2u << rb) - 1u)) + __popc(cr & ~((1u << rb) - 1u));
+        }
+        int nl = 0;
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    int t = __shfl_up_sync(FULLMASK, incl, o);
-                    if (lane >= o) incl += t;
-                }
-                base = incl - nev;
-                total = __shfl_sync(FULLMASK, incl, 31);
+        for (int p = 0; p < KPL; ++p) nl += nev[p];
+        int base = 0, total = 0;
+        if (__any_sync(FULLMASK, nl > 0)) {
+            int incl = nl;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int t = __shfl_up_sync(FULLMASK, incl, o);
+                if (lane >= o) incl += t;
             }
-            // lanes are served in contiguous groups whose events fit the queue (a lane has at
-            // most KCT_ROWS + 1 <= EV_CAP events, so every group makes progress)
-            for (int lo_lane = 0; lo_lane < 32;) {
-                int hi_lane = 32, e0 = 0;
-                if (total > 0) {
-                    const int incl = base + nev;
-                    const int base_lo = __shfl_sync(FULLMASK, base, lo_lane);
-                    const unsigned fit = __ballot_sync(FULLMASK, lane >= lo_lane && incl - base_lo <= EV_CAP);
-                    hi_lane = 32 - __clz(fit);
-                    const int ne = __shfl_sync(FULLMASK, incl, hi_lane - 1) - base_lo;
-                    e0 = base - base_lo;
-                    // 1) queue the group's crossing planes (frame-transformed parameters)
-                    if (lane >= lo_lane && lane < hi_lane && nev) {
-                        for (int b = 0; b <= R; ++b) {
-                            if (!((cross >> b) & 1u)) continue;
+            base = incl - nl;
+            total = __shfl_sync(FULLMASK, incl, 31);
+        }
+        // lanes are served in contiguous groups whose events fit the queue (a lane has at
+        // most KPL * KCT_ROWS <= EV_CAP events, so every group makes progress)
+        for (int lo_lane = 0; lo_lane < 32;) {
+            int hi_lane = 32, e0 = 0;
+            if (total > 0) {
+                const int incl = base + nl;
+                const int base_lo = __shfl_sync(FULLMASK, base, lo_lane);
+                const unsigned fit = __ballot_sync(FULLMASK, lane >= lo_lane && incl - base_lo <= EV_CAP);
+                hi_lane = 32 - __clz(fit);
+                const int ne = __shfl_sync(FULLMASK, incl, hi_lane - 1) - base_lo;
+                e0 = base - base_lo;
+                // 1) queue the group's crossing planes (frame-transformed parameters)
+                if (lane >= lo_lane && lane < hi_lane && nl) {
+                    int ep = e0;
+#pragma unroll
+                    for (int p = 0; p < KPL; ++p) {
+                        const int k = kbase + p * 32 + lane;
+                        const float zc = fmaf((float)k, az, G.z0) - V.sz;
+                        const float zs = zc * V.sgv;
+                        const float off0 = C.tc * (-fmaf(V.gv, zc * C.itc, V.cv - ((float)m_first[p] - 0.5f))) * V.inv_agv;
+                        const float p1_0 = ((float)m_first[p] - 0.5f - V.cv) * V.inv_agv;
+                        const int rb = (R[p] + 1) >> 1;
+                        const unsigned mbot = cross[p] & ((2u << rb) - 1u), mtop = cross[p] & ~((1u << rb) - 1u);
+                        const int nbot = __popc(mbot);
+                        for (unsigned m = cross[p]; m; m &= m - 1u) {
+                            const int b = __ffs(m) - 1;
                             const float p0 = fmaf(0.5f, az, fmaf((float)b, dp0, off0)), p1 = fmaf((float)b, dp1, p1_0);
                             if (b <= rb) {
-                                const int q = e0 + __popc(mbot & ((1u << b) - 1u));
+                                const int q = ep + __popc(mbot & ((1u << b) - 1u));
                                 ws->ev_p0[q] = p0;
                                 ws->ev_p1[q] = p1;
                                 ws->ev_zs[q] = zs;
                             }
                             if (b >= rb) {
-                                const int q = e0 + nbot + __popc(mtop & ((1u << b) - 1u));
+                                const int q = ep + nbot + __popc(mtop & ((1u << b) - 1u));
                                 ws->ev_p0[q] = az - p0;
                                 ws->ev_p1[q] = -p1;
                                 ws->ev_zs[q] = -zs;
                             }
                         }
+                        ep += nev[p];
                     }
-                    __syncwarp();
-                    // 2) the whole warp evaluates the events (cut moments at the crossing depths)
-                    for (int e = lane; e < ne; e += 32) {
-                        const float p0 = ws->ev_p0[e], p1 = ws->ev_p1[e];
-                        const float p1s = (fabsf(p1) < 1e-30f) ? copysignf(1e-30f, p1) : p1;
-                        const Mom full_m = Mom{fa.x, fa.y, fa.z, fa.w, fb.x};
-                        const float tau0 = -p0 / p1s, tau1 = (az - p0) / p1s;
-                        const Mom zero_m = Mom{0.f, 0.f, 0.f, 0.f, 0.f};
-                        // A plane usually leaves through one face only, so one of the two depths
-                        // lies inside H_n's depth range: one call site serves every lane (a
-                        // second one only for planes that cross both faces within H_n).
-                        const bool in0 = tau0 > tlo && tau0 < thi, in1 = tau1 > tlo && tau1 < thi;
-                        Mom ca = zero_m, cb = zero_m;
-                        if (in0 || in1) ca = cut_moments_call(ws->pt[c], ws->px[c], ws->nv[c], in0 ? tau0 : tau1, C.tc, C.xc);
-                        if (in0 && in1) cb = cut_moments_call(ws->pt[c], ws->px[c], ws->nv[c], tau1, C.tc, C.xc);
-                        const Mom c0 = in0 ? ca : (tau0 <= tlo) ? zero_m : full_m;
-                        const Mom c1 = in1 ? (in0 ? cb : ca) : (tau1 <= tlo) ? zero_m : full_m;
-                        float gv, gq;
-                        g_cross_from(az, c0, c1, full_m, p0, p1, p1s, ws->ev_zs[e], gv, gq);
-                        ws->res_v[e] = gv;
-                        ws->res_q[e] = gq;
-                    }
-                    __syncwarp();
                 }
-                // 3) pairs of the group's voxels with detector column n
-                if (lane >= lo_lane && lane < hi_lane && R > 0) {
-                    const int n = cstart + c;
+                __syncwarp();
+                // 2) the whole warp evaluates the events (cut moments at the crossing depths)
+                for (int e = lane; e < ne; e += 32) {
+                    const float p0 = ws->ev_p0[e], p1 = ws->ev_p1[e];
+                    const float p1s = (fabsf(p1) < 1e-30f) ? copysignf(1e-30f, p1) : p1;
+                    const Mom full_m = Mom{fa.x, fa.y, fa.z, fa.w, fb.x};
+                    const float tau0 = -p0 / p1s, tau1 = (az - p0) / p1s;
+                    const Mom zero_m = Mom{0.f, 0.f, 0.f, 0.f, 0.f};
+                    // A plane usually leaves through one face only, so one of the two depths
+                    // lies inside H_n's depth range: one call site serves every lane (a
+                    // second one only for planes that cross both faces within H_n).
+                    const bool in0 = tau0 > tlo && tau0 < thi, in1 = tau1 > tlo && tau1 < thi;
+                    Mom ca = zero_m, cb = zero_m;
+                    if (in0 || in1) ca = cut_moments_call(ws->pt[c], ws->px[c], ws->nv[c], in0 ? tau0 : tau1, C.tc, C.xc);
+                    if (in0 && in1) cb = cut_moments_call(ws->pt[c], ws->px[c], ws->nv[c], tau1, C.tc, C.xc);
+                    const Mom c0 = in0 ? ca : (tau0 <= tlo) ? zero_m : full_m;
+                    const Mom c1 = in1 ? (in0 ? cb : ca) : (tau1 <= tlo) ? zero_m : full_m;
+                    float gv, gq;
+                    g_cross_from(az, c0, c1, full_m, p0, p1, p1s, ws->ev_zs[e], gv, gq);
+                    ws->res_v[e] = gv;
+                    ws->res_q[e] = gq;
+                }
+                __syncwarp();
+            }
+            // 3) pairs of the group's voxels with detector column n
+            if (lane >= lo_lane && lane < hi_lane) {
+                const int n = cstart + c;
+                int ep = e0;
+#pragma unroll
+                for (int p = 0; p < KPL; ++p) {
+                    const int k = kbase + p * 32 + lane;
+                    const float zc = fmaf((float)k, az, G.z0) - V.sz;
+                    const float bc = zc * C.itc;
+                    const float zs = zc * V.sgv;
+                    const float D2 = fmaf(C.tc, C.tc, fmaf(C.xc, C.xc, zc * zc));
+                    const float off0 = C.tc * (-fmaf(V.gv, bc, V.cv - ((float)m_first[p] - 0.5f))) * V.inv_agv;
+                    const float p1_0 = ((float)m_first[p] - 0.5f - V.cv) * V.inv_agv;
+                    const int rb = (R[p] + 1) >> 1;
+                    const unsigned mbot = cross[p] & ((2u << rb) - 1u), mtop = cross[p] & ~((1u << rb) - 1u);
+                    const int nbot = __popc(mbot);
 #pragma unroll 1
-                    for (int r = 0; r < R; ++r) {
-                        const int m = m_first + r;
+                    for (int r = 0; r < R[p]; ++r) {
+                        const int m = m_first[p] + r;
                         const unsigned bl = 1u << r, bh = 2u << r;
                         float pv, pq;
-                        if (!((cross | zero | full) & (bl | bh))) {
+                        if (!((cross[p] | zero[p] | full[p]) & (bl | bh))) {
                             // both planes inside: height dp0 + dp1 t' centred at s0 + s1 t'
                             const float s0 = C.tc * (-fmaf(V.gv, bc, V.cv - (float)m)) * V.inv_agv;
                             const float s1 = ((float)m - V.cv) * V.inv_agv;
@@ -273,14 +309,14 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
                                 const int b = r + h;
                                 const unsigned bit = 1u << b;
                                 float p0 = fmaf(0.5f, az, fmaf((float)b, dp0, off0)), p1 = fmaf((float)b, dp1, p1_0);
-                                if (zero & bit) { p0 = 0.f; p1 = 0.f; }
-                                if (full & bit) { p0 = az; p1 = 0.f; }
+                                if (zero[p] & bit) { p0 = 0.f; p1 = 0.f; }
+                                if (full[p] & bit) { p0 = az; p1 = 0.f; }
                                 // the linear form in the row's frame is evaluated by every lane (no
                                 // divergence on the frame); crossing planes then take the queued result
                                 g_lin(az, top ? az - p0 : p0, top ? -p1 : p1, top ? -zs : zs, fa.x, fa.y, fa.z, fa.w, fb.x,
                                       g[h][0], g[h][1]);
-                                if (cross & bit) {
-                                    const int q = top ? e0 + nbot + __popc(mtop & (bit - 1u)) : e0 + __popc(mbot & (bit - 1u));
+                                if (cross[p] & bit) {
+                                    const int q = top ? ep + nbot + __popc(mtop & (bit - 1u)) : ep + __popc(mbot & (bit - 1u));
                                     g[h][0] = ws->res_v[q];
                                     g[h][1] = ws->res_q[q];
                                 }
@@ -288,14 +324,19 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
                             pv = top ? g[0][0] - g[1][0] : g[1][0] - g[0][0];
                             pq = top ? g[0][1] - g[1][1] : g[1][1] - g[0][1];
                         }
-                        if (pv > vtiny) sink.pair(pass, n, m, pair_weight(pv, pq, D2));
+                        if (pv > vtiny) sink.pair(p, n, m, pair_weight(pv, pq, D2));
                     }
+                    ep += nev[p];
                 }
-                if (total > 0) __syncwarp();
-                lo_lane = hi_lane;
             }
+            if (total > 0) __syncwarp();
+            lo_lane = hi_lane;
         }
-        if (act) sink.end(pass, k);
+    }
+#pragma unroll
+    for (int p = 0; p < KPL; ++p) {
+        const int k = kbase + p * 32 + lane;
+        if (k < G.nz) sink.end(p, k);
     }
 }
 
@@ -431,14 +472,22 @@ struct FwdSink {
     Tile T;
     float* __restrict__ Sg;        // global output of the view
     int nu, col, kbase;
-    float mu;
-    __device__ __forceinline__ void begin(int, int k) { mu = mu_s[(k - kbase) * NCOLS + col]; }
+    float mu[KPL];
+    __device__ __forceinline__ void begin(int p, int k) {
+#pragma unroll
+        for (int q = 0; q < KPL; ++q)
+            if (q == p) mu[q] = mu_s[(k - kbase) * NCOLS + col];
+    }
     __device__ __forceinline__ void end(int, int) {}
-    __device__ __forceinline__ void pair(int, int n, int m, float W) {
-        if (mu == 0.f) return;
+    __device__ __forceinline__ void pair(int p, int n, int m, float W) {
+        float mp = 0.f;
+#pragma unroll
+        for (int q = 0; q < KPL; ++q)
+            if (q == p) mp = mu[q];
+        if (mp == 0.f) return;
         const int du = n - T.u0, dv = m - T.v0;
-        if (T.ok && (unsigned)du < (unsigned)T.w && (unsigned)dv < (unsigned)T.h) atomicAdd(&tile[dv * T.w + du], mu * W);
-        else atomicAdd(&Sg[(size_t)m * nu + n], SCALING >= 0 ? mu * W * pixel_factor<(SCALING > 0)>(*V, n, m) : mu * W);
+        if (T.ok && (unsigned)du < (unsigned)T.w && (unsigned)dv < (unsigned)T.h) atomicAdd(&tile[dv * T.w + du], mp * W);
+        else atomicAdd(&Sg[(size_t)m * nu + n], SCALING >= 0 ? mp * W * pixel_factor<(SCALING > 0)>(*V, n, m) : mp * W);
     }
 };
 
