@@ -47,6 +47,7 @@ struct WarpSmem {
     float4 fa[KCT_CB];             // exact: moments of H_n m1, mt, mtt, ml; relaxed: A_n, t_n, 1/t_n, -
     float4 fb[KCT_CB];             // exact: mlt, t'-range of H_n (lo, hi), -
     float2 fr[KCT_CB];             // exact: 1 / depth at the two ends of that range
+    float eg[KCT_CB][8][5];        // exact: Green terms of each whole edge of H_n (a, t, x, tt, tx)
     float ev_p0[EV_CAP], ev_p1[EV_CAP], ev_zs[EV_CAP];
     float res_v[EV_CAP], res_q[EV_CAP];
 };
@@ -89,11 +90,39 @@ KCT_HD RowPlane row_boundary(const View& V, const Grid& G, const Column& C, cons
     return r;
 }
 
-// Moments (1, t', t'^2, lambda, lambda t') of H_n ∩ {t' < tau} from the vertices of H_n.
-// Not inlined: the polygon clipping exists once in the code and its callers stay small.
-__device__ __noinline__ Mom cut_moments_call(const float* pt, const float* px, int nv, float tau, float tc,
-                                             float xc) {
-    return normalise(polygon_cut<true>(pt, px, nv, tau), tc, xc);
+// Moments (1, t', t'^2, lambda, lambda t') of H_n ∩ {t' < tau} from the vertices of H_n:
+// Green's theorem over the boundary of the cut, i.e. the edges below tau (their whole-edge
+// terms are precomputed in eg), the clipped parts of the two edges that cross t' = tau, and
+// the chord along t' = tau. Same sums in the same order as polygon_cut.
+// Not inlined: the clipping exists once in the code and its callers stay small.
+__device__ __noinline__ Mom cut_moments_call(const float* pt, const float* px, const float (*eg)[5], int nv,
+                                             float tau, float tc, float xc) {
+    Mom5 m = mom_zero();
+    float xt = 0.f, xx = 0.f, nt = 0.f, nx = 0.f;
+    bool hx = false, hn = false;
+    for (int e = 0; e < nv; ++e) {
+        const int f = (e + 1 == nv) ? 0 : e + 1;
+        const float at = pt[e], bt = pt[f];
+        const float La = at - tau, Lb = bt - tau;
+        if (La < 0.f && Lb < 0.f) {
+            m.a += eg[e][0];
+            m.t += eg[e][1];
+            m.x += eg[e][2];
+            m.tt += eg[e][3];
+            m.tx += eg[e][4];
+        } else if ((La < 0.f) != (Lb < 0.f)) {
+            const float ax = px[e], bx = px[f];
+            float s0 = 0.f, s1 = 1.f;
+            clip_param(La, Lb, s0, s1);
+            seg_part<true>(m, at, ax, bt, bx, s0, s1);
+            const float ss = La / (La - Lb);
+            const float ct = fmaf(ss, bt - at, at), cx = fmaf(ss, bx - ax, ax);
+            if (La < 0.f) { xt = ct; xx = cx; hx = true; }
+            else { nt = ct; nx = cx; hn = true; }
+        }
+    }
+    if (hx && hn) seg_acc<true>(m, xt, xx, nt, nx);
+    return normalise(m, tc, xc);
 }
 
 // Volume and first moment along D of {(t', xi') in H_n, 0 < height < clamp(p0 + p1 t', 0, az)}
@@ -262,8 +291,8 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
                     // second one only for planes that cross both faces within H_n).
                     const bool in0 = tau0 > tlo && tau0 < thi, in1 = tau1 > tlo && tau1 < thi;
                     Mom ca = zero_m, cb = zero_m;
-                    if (in0 || in1) ca = cut_moments_call(ws->pt[c], ws->px[c], ws->nv[c], in0 ? tau0 : tau1, C.tc, C.xc);
-                    if (in0 && in1) cb = cut_moments_call(ws->pt[c], ws->px[c], ws->nv[c], tau1, C.tc, C.xc);
+                    if (in0 || in1) ca = cut_moments_call(ws->pt[c], ws->px[c], ws->eg[c], ws->nv[c], in0 ? tau0 : tau1, C.tc, C.xc);
+                    if (in0 && in1) cb = cut_moments_call(ws->pt[c], ws->px[c], ws->eg[c], ws->nv[c], tau1, C.tc, C.xc);
                     const Mom c0 = in0 ? ca : (tau0 <= tlo) ? zero_m : full_m;
                     const Mom c1 = in1 ? (in0 ? cb : ca) : (tau1 <= tlo) ? zero_m : full_m;
                     float gv, gq;
@@ -399,6 +428,16 @@ __device__ __noinline__ void build_column_cut(const View* Vp, const Column* Cp, 
         ws->fa[c] = make_float4(f.m1, f.mt, f.mtt, f.ml);
         ws->fb[c] = make_float4(f.mlt, tlo, thi, 0.f);
         ws->fr[c] = make_float2(1.0f / (C.tc + tlo), 1.0f / (C.tc + thi));
+        for (int e = 0; e < nv; ++e) {
+            const int g = (e + 1 == nv) ? 0 : e + 1;
+            Mom5 m = mom_zero();
+            seg_acc<true>(m, pt[e], px[e], pt[g], px[g]);
+            ws->eg[c][e][0] = m.a;
+            ws->eg[c][e][1] = m.t;
+            ws->eg[c][e][2] = m.x;
+            ws->eg[c][e][3] = m.tt;
+            ws->eg[c][e][4] = m.tx;
+        }
     }
 }
 
