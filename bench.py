@@ -34,15 +34,20 @@ UNIT = "Gvoxel·views/s"
 # restricted to 8 of its views (python bench.py --profile-case cvp512 --views 8 ...; see
 # profiles/projector_kernels_cvp512_8views.md):
 #   flop_per_vv  FP32 operations (thread-level FADD + FMUL + 2 FFMA) per voxel-view,
+#   warp_per_vv  warp instructions issued per voxel-view, simt: active lanes per instruction / 32,
 #   dram_8       DRAM bytes read + written by that 8-view launch.
 # A full 496-view launch processes 62x the voxel-views; the forward kernel re-reads the
 # volume once per chunk of 16 views and adds one projection per view, the adjoint reads one
 # projection tile per view and writes the volume once, so traffic is scaled as below.
 NCU = {
-    "exact project": {"flop_per_vv": 999.8, "dram_read_8": 5.808e8, "dram_write_8": 3.371e7},
-    "exact backproject": {"flop_per_vv": 1053.2, "dram_read_8": 6.111e7, "dram_write_8": 4.958e8},
-    "relaxed project": {"flop_per_vv": 165.5, "dram_read_8": 5.750e8, "dram_write_8": 3.268e7},
-    "relaxed backproject": {"flop_per_vv": 188.0, "dram_read_8": 4.954e7, "dram_write_8": 4.889e8},
+    "exact project": {"flop_per_vv": 1015.2, "warp_per_vv": 125.3, "simt": 0.56,
+                      "dram_read_8": 5.7995e8, "dram_write_8": 3.3333e7},
+    "exact backproject": {"flop_per_vv": 1077.4, "warp_per_vv": 129.2, "simt": 0.57,
+                          "dram_read_8": 5.6781e7, "dram_write_8": 4.9357e8},
+    "relaxed project": {"flop_per_vv": 168.9, "warp_per_vv": 31.0, "simt": 0.55,
+                        "dram_read_8": 5.7136e8, "dram_write_8": 3.1922e7},
+    "relaxed backproject": {"flop_per_vv": 201.0, "warp_per_vv": 35.1, "simt": 0.57,
+                            "dram_read_8": 4.8661e7, "dram_write_8": 4.8807e8},
 }
 
 
@@ -426,8 +431,15 @@ def run_kct(args):
     achieved = (flop_vv * geom.voxel_views / (dom_ms / 1e3) / 1e12) if flop_vv else None
     traffic = full_launch_traffic(name, geom.nviews) if args.workload == WORKLOAD else None
     fp32_probe = probe_fp32_tflops()
+    # the same kernel against the instruction-issue limit (4 warp instructions per SM and cycle)
+    wpv = NCU[name]["warp_per_vv"] if args.workload == WORKLOAD else None
+    clk = (clocks.get("sm_mhz") or max_mhz) * 1e6
+    issue = ({"warp_inst_per_voxel_view": wpv, "achieved_per_s": wpv * geom.voxel_views / (dom_ms / 1e3),
+              "peak_per_s": sms * 4 * clk, "frac": wpv * geom.voxel_views / (dom_ms / 1e3) / (sms * 4 * clk),
+              "simt_efficiency": NCU[name]["simt"], "basis": "ncu warp instruction count x event-timed launch"}
+             if wpv else None)
     roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "measured_fp32_fma_tflops": fp32_probe,
+                "measured_fp32_fma_tflops": fp32_probe, "issue": issue,
                 "frac": (achieved / peak_tflops) if achieved else None, "traffic": traffic,
                 "traffic_unit": "bytes per launch (ncu, 8-view capture scaled to the full launch)",
                 "launch_ms": dom_ms, "flop_per_voxel_view": flop_vv,
