@@ -276,6 +276,13 @@ def run_cgls(dev, scaling: str, max_iter: int, tol: float = 1e-3):
     return out
 
 
+def bench_config(args, world: int) -> dict:
+    """The workload description both arms report."""
+    return {"workload": WORKLOAD_DESC, "step": "project + backproject, near-exact and relaxed variants",
+            "scaling": args.scaling, "parallelism": f"replicas x{world}",
+            "l2": "inputs (0.54 GB volume, 2.35 GB projections) larger than L2; no flush"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -296,7 +303,7 @@ def run_reference(args):
            "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
-           "config": {"workload": WORKLOAD_DESC, "variant": "exact", "scaling": args.scaling},
+           "config": bench_config(args, world),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -450,10 +457,7 @@ def run_kct(args):
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic (seeded ellipsoid phantom; U[0,1) projections for the adjoint)",
-           "config": {"workload": WORKLOAD_DESC,
-                      "step": "project + backproject, near-exact and relaxed variants",
-                      "scaling": args.scaling, "parallelism": f"replicas x{world}",
-                      "l2": "inputs (0.54 GB volume, 2.35 GB projections) larger than L2; no flush"},
+           "config": bench_config(args, world),
            "variants": per, "roofline": roofline,
            "cpu_baseline": {"value": cb_val / 1e9, "unit": UNIT, "cores": cb_threads, "kind": "oracle",
                             "sample": cb_desc},
