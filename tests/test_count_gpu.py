@@ -18,9 +18,10 @@ pytestmark = pytest.mark.gpu
 
 @pytest.mark.parametrize("vname,variant", [("exact", oracle.EXACT), ("relaxed", oracle.RELAXED)])
 def test_pair_count_matches_oracle_nonzeros(vname, variant):
-    # generic sizes (odd row count, pitch unrelated to the voxel size) so that no voxel face
-    # projects exactly onto a row boundary, where a zero-length overlap could round either way
-    g = inputs.make_geometry((4, 4, 4), (0.93, 0.93, 0.93), (10, 11), (1.07, 1.07), 8, 61.7, 93.1, 360.0)
+    # generic sizes (odd pixel counts, pitch unrelated to the voxel size, 7 views) so that no
+    # voxel edge projects exactly onto a pixel boundary, where a zero-size cut could round
+    # either way (the relaxed variant keeps any positive overlap)
+    g = inputs.make_geometry((4, 4, 4), (0.93, 0.93, 0.93), (11, 11), (1.07, 1.07), 7, 61.7, 93.1, 360.0)
     A = dense_matrix(g, variant).reshape(g.nviews, g.nv, g.nu, -1)
     vol = g.ax * g.ay * g.az
     strict = loose = 0
