@@ -1,6 +1,7 @@
 // cvp_kernels.cuh -- brick-tiled CUDA kernels of the cutting voxel projector (sm_103a).
 //
-// A thread block owns a brick of BX x BY voxel columns and SEG = 64 voxels along x_3.
+// A thread block owns a brick of BX x BY voxel columns and Brick<VARIANT>::Z voxels along x_3
+// (one or two runs of SEG = 64).
 //  * Forward: the brick's attenuation values are staged in shared memory once; for each view
 //    of the block's chunk, the voxel-pixel weights are accumulated into a shared-memory
 //    detector tile that covers the brick's footprint, then the tile is added to the global
@@ -33,11 +34,22 @@ constexpr int NCOLS = BX * BY;
 constexpr int NWARP = 8;           // warps per block
 constexpr int NTHREADS = 32 * NWARP;
 // Blocks per SM: 2 for the near-exact kernels (their register need), 3 for the relaxed ones
-// (measured 21 % faster than with 2); the shared memory of a block (static part + SEG * NCOLS +
-// TILE_CAP floats) is sized so that 3 fit.
+// (measured 21 % faster than with 2); the shared memory of a block (static part +
+// Brick::DYN_FLOATS floats) is sized accordingly.
 constexpr int EV_CAP = 64;         // crossing events queued per warp and round (>= KPL * KCT_ROWS)
 constexpr int KCT_ROWS = 32;       // row boundaries of one voxel (its footprint spans <= 31 rows)
-constexpr int TILE_CAP = 7168;     // floats of the shared detector tile
+constexpr int TILE_CAP = 7168;     // floats of the shared detector tile (relaxed kernels)
+
+// Brick height along x_3 per variant: the near-exact kernels take two runs of SEG voxels per
+// column-cut build (the build is about a fifth of their time), the relaxed ones one run (so
+// that three of their blocks fit on an SM).
+template <int VARIANT>
+struct Brick {
+    static constexpr int RUNS = VARIANT == 0 ? 2 : 1;
+    static constexpr int Z = SEG * RUNS;                       // voxels along x_3
+    static constexpr int TILE = VARIANT == 0 ? 12288 : TILE_CAP;   // floats of the detector tile
+    static constexpr int DYN_FLOATS = Z * NCOLS + TILE;        // dynamic shared memory
+};
 constexpr int VIEW_CHUNK = 16;     // default views per forward block (a plan may tune it)
 constexpr int MAX_VIEW_CHUNK = 64; // largest views per forward block a plan accepts
 constexpr int TUNE_VIEWS = 64;     // views the forward tuning launches cover
@@ -444,11 +456,12 @@ __device__ __noinline__ void build_column_cut(const View* Vp, const Column* Cp, 
     }
 }
 
-// All pairs of voxels kbase .. kbase + SEG - 1 of column (i, j) in view V (in shared memory).
-// Called by all 32 lanes of a warp with the same arguments.
+// All pairs of voxels kbase .. kbase + runs * SEG - 1 of column (i, j) in view V (in shared
+// memory): each column cut is built once and used by `runs` runs of SEG voxels; the sink is
+// told when a run ends. Called by all 32 lanes of a warp with the same arguments.
 template <int VARIANT, class Sink>
-__device__ __forceinline__ void warp_column(const View& V, const Grid& G, int i, int j, int kbase, int lane,
-                                            WarpSmem* ws, Sink& sink, int* err) {
+__device__ __forceinline__ void warp_column(const View& V, const Grid& G, int i, int j, int kbase, int runs,
+                                            int lane, WarpSmem* ws, Sink& sink, int* err) {
     Column C;
     if (!column_setup(V, G, i, j, C)) return;
     if (C.n_last - C.n_first + 2 > KCT_MAX_SPAN) {
@@ -460,17 +473,24 @@ __device__ __forceinline__ void warp_column(const View& V, const Grid& G, int i,
         __syncwarp();              // the previous readers of ws are done
         if (lane < ncol) build_column_cut(&V, &C, G.az, cstart + lane, VARIANT, ws, lane);
         __syncwarp();
-        if (VARIANT == 1) relaxed_voxels(V, G, C, cstart, ncol, kbase, lane, ws, sink, err);
-        else exact_voxels(V, G, C, cstart, ncol, kbase, lane, ws, sink, err);
+#pragma unroll 1
+        for (int r = 0; r < runs; ++r) {
+            const int kb = kbase + r * SEG;
+            if (kb >= G.nz) break;
+            if (VARIANT == 1) relaxed_voxels(V, G, C, cstart, ncol, kb, lane, ws, sink, err);
+            else exact_voxels(V, G, C, cstart, ncol, kb, lane, ws, sink, err);
+            sink.end_run(r);
+        }
     }
 }
 
-// Detector window covered by the brick [i0, i0+BX) x [j0, j0+BY) x [k0, k0+SEG) in view V:
-// the bounding box of the projected corners (u does not depend on x_3), one pixel of margin.
-__device__ __forceinline__ Tile brick_tile(const View& V, const Grid& G, int i0, int j0, int k0) {
+// Detector window covered by the brick [i0, i0+BX) x [j0, j0+BY) x [k0, k0+bz) in view V:
+// the bounding box of the projected corners (u does not depend on x_3), one pixel of margin,
+// if it holds at most `cap` pixels.
+__device__ __forceinline__ Tile brick_tile(const View& V, const Grid& G, int i0, int j0, int k0, int bz, int cap) {
     const float xs[2] = {G.x0 + (i0 - 0.5f) * G.ax, G.x0 + (min(i0 + BX, G.nx) - 0.5f) * G.ax};
     const float ys[2] = {G.y0 + (j0 - 0.5f) * G.ay, G.y0 + (min(j0 + BY, G.ny) - 0.5f) * G.ay};
-    const float zs[2] = {G.z0 + (k0 - 0.5f) * G.az - V.sz, G.z0 + (min(k0 + SEG, G.nz) - 0.5f) * G.az - V.sz};
+    const float zs[2] = {G.z0 + (k0 - 0.5f) * G.az - V.sz, G.z0 + (min(k0 + bz, G.nz) - 0.5f) * G.az - V.sz};
     float umin = 3e38f, umax = -3e38f, vmin = 3e38f, vmax = -3e38f;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -495,7 +515,7 @@ __device__ __forceinline__ Tile brick_tile(const View& V, const Grid& G, int i0,
     T.w = u1 - T.u0 + 1;
     T.h = v1 - T.v0 + 1;
     if (T.w <= 0 || T.h <= 0) T.w = T.h = 0;
-    T.ok = (T.w > 0 && (long)T.w * T.h <= TILE_CAP) ? 1 : 0;
+    T.ok = (T.w > 0 && (long)T.w * T.h <= cap) ? 1 : 0;
     return T;
 }
 
@@ -509,7 +529,7 @@ __device__ __forceinline__ Tile brick_tile(const View& V, const Grid& G, int i0,
 template <int SCALING>
 struct FwdSink {
     const View* V;
-    const float* mu_s;             // brick attenuation values, [SEG][BY][BX] in shared memory
+    const float* mu_s;             // brick attenuation values, [Brick::Z][BY][BX] in shared memory
     float* tile;
     Tile T;
     float* __restrict__ Sg;        // global output of the view
@@ -521,6 +541,7 @@ struct FwdSink {
             if (q == p) mu[q] = mu_s[(k - kbase) * NCOLS + col];
     }
     __device__ __forceinline__ void end(int, int) {}
+    __device__ __forceinline__ void end_run(int) {}
     __device__ __forceinline__ void pair(int p, int n, int m, float W) {
         float mp = 0.f;
 #pragma unroll
@@ -542,9 +563,19 @@ struct BwdSink {
     Tile T;
     const float* __restrict__ yg;
     int nu;
+    float* acc_col;                // the column's accumulators in shared memory, one per voxel of the brick
+    int lane;
     float acc[KPL];
     __device__ __forceinline__ void begin(int, int) {}
     __device__ __forceinline__ void end(int, int) {}
+    // voxel kbase + r * SEG + p * 32 + lane of the brick
+    __device__ __forceinline__ void end_run(int r) {
+#pragma unroll
+        for (int p = 0; p < KPL; ++p) {
+            acc_col[r * SEG + p * 32 + lane] += acc[p];
+            acc[p] = 0.f;
+        }
+    }
     __device__ __forceinline__ void pair(int p, int n, int m, float W) {
         const int du = n - T.u0, dv = m - T.v0;
         const float y = (T.ok && (unsigned)du < (unsigned)T.w && (unsigned)dv < (unsigned)T.h)
@@ -560,6 +591,7 @@ struct CountSink {
     unsigned long long n;
     __device__ __forceinline__ void begin(int, int) {}
     __device__ __forceinline__ void end(int, int) {}
+    __device__ __forceinline__ void end_run(int) {}
     __device__ __forceinline__ void pair(int, int, int, float W) { n += (W > 0.f) ? 1ull : 0ull; }
 };
 
@@ -579,7 +611,7 @@ __device__ __forceinline__ void brick_origin(const Grid& G, int& i0, int& j0) {
 // SCALING 0 / 1 multiplies by the cos / exact pixel factor while the tile is flushed;
 // SCALING < 0 leaves the unscaled sums of Eq. cvpsu. out must be zeroed (or hold the values
 // to add to) before the launch.
-// Dynamic shared memory: SEG * NCOLS + TILE_CAP floats.
+// Dynamic shared memory: Brick<VARIANT>::DYN_FLOATS floats.
 template <int VARIANT, int SCALING>
 __global__ void __launch_bounds__(NTHREADS, VARIANT == 1 ? 3 : 2) fwd_kernel(const View* __restrict__ views, Grid G,
                                                           const float* __restrict__ vol, float* __restrict__ out,
@@ -587,17 +619,18 @@ __global__ void __launch_bounds__(NTHREADS, VARIANT == 1 ? 3 : 2) fwd_kernel(con
                                                           int* err) {
     extern __shared__ float dyn[];
     __shared__ BlockSmem bs;
+    using B = Brick<VARIANT>;
     float* mu_s = dyn;
-    float* tile = dyn + SEG * NCOLS;
+    float* tile = dyn + B::Z * NCOLS;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int i0, j0;
     brick_origin(G, i0, j0);
-    const int kbase = blockIdx.y * SEG;
+    const int kbase = blockIdx.y * B::Z;
     const int nchunk = (G.nviews + view_chunk - 1) / view_chunk;
     const int chunk = blockIdx.z % nchunk, batch = blockIdx.z / nchunk;
     vol += batch * vstride;
     out += batch * pstride;
-    for (int q = threadIdx.x; q < SEG * NCOLS; q += NTHREADS) {
+    for (int q = threadIdx.x; q < B::Z * NCOLS; q += NTHREADS) {
         const int kk = q / NCOLS, c = q % NCOLS;
         const int i = i0 + c % BX, j = j0 + c / BX, k = kbase + kk;
         mu_s[q] = (i < G.nx && j < G.ny && k < G.nz) ? __ldg(&vol[((size_t)k * G.ny + j) * G.nx + i]) : 0.f;
@@ -607,7 +640,7 @@ __global__ void __launch_bounds__(NTHREADS, VARIANT == 1 ? 3 : 2) fwd_kernel(con
         __syncthreads();
         if (threadIdx.x == 0) {
             bs.V = views[view];
-            bs.T = brick_tile(bs.V, G, i0, j0, kbase);
+            bs.T = brick_tile(bs.V, G, i0, j0, kbase, B::Z, B::TILE);
         }
         __syncthreads();
         const Tile T = bs.T;
@@ -619,7 +652,7 @@ __global__ void __launch_bounds__(NTHREADS, VARIANT == 1 ? 3 : 2) fwd_kernel(con
             const int i = i0 + c % BX, j = j0 + c / BX;
             if (i >= G.nx || j >= G.ny) continue;
             FwdSink<SCALING> s{&bs.V, mu_s, tile, T, Sv, G.nu, c, kbase, 0.f};
-            warp_column<VARIANT>(bs.V, G, i, j, kbase, lane, &bs.ws[warp], s, err);
+            warp_column<VARIANT>(bs.V, G, i, j, kbase, B::RUNS, lane, &bs.ws[warp], s, err);
         }
         __syncthreads();
         if (T.ok)
@@ -635,7 +668,7 @@ __global__ void __launch_bounds__(NTHREADS, VARIANT == 1 ? 3 : 2) fwd_kernel(con
 
 // Adjoint. grid: (bricks in x1 x2, segments along x3, batch); every block loops over all
 // views, staging F y of the brick's footprint in shared memory per view.
-// Dynamic shared memory: SEG * NCOLS + TILE_CAP floats.
+// Dynamic shared memory: Brick<VARIANT>::DYN_FLOATS floats.
 template <int VARIANT, int SCALING>
 __global__ void __launch_bounds__(NTHREADS, VARIANT == 1 ? 3 : 2) bwd_kernel(const View* __restrict__ views, Grid G,
                                                           const float* __restrict__ y, float* __restrict__ vol,
@@ -643,20 +676,21 @@ __global__ void __launch_bounds__(NTHREADS, VARIANT == 1 ? 3 : 2) bwd_kernel(con
                                                           int* err) {
     extern __shared__ float dyn[];
     __shared__ BlockSmem bs;
-    float* acc_s = dyn;                 // [NCOLS][SEG]
-    float* tile = dyn + SEG * NCOLS;
+    using B = Brick<VARIANT>;
+    float* acc_s = dyn;                 // [NCOLS][B::Z]
+    float* tile = dyn + B::Z * NCOLS;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int i0, j0;
     brick_origin(G, i0, j0);
-    const int kbase = blockIdx.y * SEG;
+    const int kbase = blockIdx.y * B::Z;
     vol += blockIdx.z * vstride;
     y += blockIdx.z * pstride;
-    for (int q = threadIdx.x; q < SEG * NCOLS; q += NTHREADS) acc_s[q] = 0.f;
+    for (int q = threadIdx.x; q < B::Z * NCOLS; q += NTHREADS) acc_s[q] = 0.f;
     for (int view = 0; view < G.nviews; ++view) {
         __syncthreads();
         if (threadIdx.x == 0) {
             bs.V = views[view];
-            bs.T = brick_tile(bs.V, G, i0, j0, kbase);
+            bs.T = brick_tile(bs.V, G, i0, j0, kbase, B::Z, B::TILE);
         }
         __syncthreads();
         const Tile T = bs.T;
@@ -670,17 +704,15 @@ __global__ void __launch_bounds__(NTHREADS, VARIANT == 1 ? 3 : 2) bwd_kernel(con
         for (int c = warp; c < NCOLS; c += NWARP) {
             const int i = i0 + c % BX, j = j0 + c / BX;
             if (i >= G.nx || j >= G.ny) continue;
-            BwdSink<SCALING> s{&bs.V, tile, T, yv, G.nu, {}};
+            BwdSink<SCALING> s{&bs.V, tile, T, yv, G.nu, acc_s + c * B::Z, lane, {}};
 #pragma unroll
             for (int p = 0; p < KPL; ++p) s.acc[p] = 0.f;
-            warp_column<VARIANT>(bs.V, G, i, j, kbase, lane, &bs.ws[warp], s, err);
-#pragma unroll
-            for (int p = 0; p < KPL; ++p) acc_s[c * SEG + p * 32 + lane] += s.acc[p];
+            warp_column<VARIANT>(bs.V, G, i, j, kbase, B::RUNS, lane, &bs.ws[warp], s, err);
         }
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < SEG * NCOLS; q += NTHREADS) {
-        const int c = q / SEG, kk = q % SEG;
+    for (int q = threadIdx.x; q < B::Z * NCOLS; q += NTHREADS) {
+        const int c = q / B::Z, kk = q % B::Z;
         const int i = i0 + c % BX, j = j0 + c / BX, k = kbase + kk;
         if (i < G.nx && j < G.ny && k < G.nz) {
             const size_t idx = ((size_t)k * G.ny + j) * G.nx + i;
@@ -697,14 +729,14 @@ __global__ void __launch_bounds__(NTHREADS, 2) count_kernel(const View* __restri
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int i0, j0;
     brick_origin(G, i0, j0);
-    const int kbase = blockIdx.y * SEG;
+    const int kbase = blockIdx.y * Brick<VARIANT>::Z;
     if (threadIdx.x == 0) bs.V = views[blockIdx.z];
     __syncthreads();
     CountSink s{0ull};
     for (int c = warp; c < NCOLS; c += NWARP) {
         const int i = i0 + c % BX, j = j0 + c / BX;
         if (i >= G.nx || j >= G.ny) continue;
-        warp_column<VARIANT>(bs.V, G, i, j, kbase, lane, &bs.ws[warp], s, err);
+        warp_column<VARIANT>(bs.V, G, i, j, kbase, Brick<VARIANT>::RUNS, lane, &bs.ws[warp], s, err);
     }
     unsigned long long v = s.n;
 #pragma unroll

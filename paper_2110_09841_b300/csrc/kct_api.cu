@@ -170,29 +170,31 @@ unsigned bricks(const Grid& G) {
     return (unsigned)(((G.nx + kct::BX - 1) / kct::BX) * ((G.ny + kct::BY - 1) / kct::BY));
 }
 
-unsigned segments(const Grid& G) { return (unsigned)((G.nz + kct::SEG - 1) / kct::SEG); }
+template <int VARIANT>
+unsigned segments(const Grid& G) { return (unsigned)((G.nz + kct::Brick<VARIANT>::Z - 1) / kct::Brick<VARIANT>::Z); }
 
-constexpr size_t kBrickDynSmem = sizeof(float) * (kct::SEG * kct::NCOLS + kct::TILE_CAP);
+template <int VARIANT>
+constexpr size_t brick_dyn_smem() { return sizeof(float) * kct::Brick<VARIANT>::DYN_FLOATS; }
 
 // opt in to more than 48 KB of shared memory per block (once per process)
 template <class K>
-cudaError_t set_dyn(K kernel, cudaError_t e) {
-    return e == cudaSuccess ? cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBrickDynSmem) : e;
+cudaError_t set_dyn(K kernel, size_t bytes, cudaError_t e) {
+    return e == cudaSuccess ? cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) : e;
 }
 
 cudaError_t brick_kernel_attributes() {
     static cudaError_t done = [] {
         cudaError_t e = cudaSuccess;
-        e = set_dyn(kct::fwd_kernel<0, 0>, e);
-        e = set_dyn(kct::fwd_kernel<0, 1>, e);
-        e = set_dyn(kct::fwd_kernel<1, 0>, e);
-        e = set_dyn(kct::fwd_kernel<1, 1>, e);
-        e = set_dyn(kct::fwd_kernel<0, -1>, e);
-        e = set_dyn(kct::fwd_kernel<1, -1>, e);
-        e = set_dyn(kct::bwd_kernel<0, 0>, e);
-        e = set_dyn(kct::bwd_kernel<0, 1>, e);
-        e = set_dyn(kct::bwd_kernel<1, 0>, e);
-        e = set_dyn(kct::bwd_kernel<1, 1>, e);
+        e = set_dyn(kct::fwd_kernel<0, 0>, brick_dyn_smem<0>(), e);
+        e = set_dyn(kct::fwd_kernel<0, 1>, brick_dyn_smem<0>(), e);
+        e = set_dyn(kct::fwd_kernel<1, 0>, brick_dyn_smem<1>(), e);
+        e = set_dyn(kct::fwd_kernel<1, 1>, brick_dyn_smem<1>(), e);
+        e = set_dyn(kct::fwd_kernel<0, -1>, brick_dyn_smem<0>(), e);
+        e = set_dyn(kct::fwd_kernel<1, -1>, brick_dyn_smem<1>(), e);
+        e = set_dyn(kct::bwd_kernel<0, 0>, brick_dyn_smem<0>(), e);
+        e = set_dyn(kct::bwd_kernel<0, 1>, brick_dyn_smem<0>(), e);
+        e = set_dyn(kct::bwd_kernel<1, 0>, brick_dyn_smem<1>(), e);
+        e = set_dyn(kct::bwd_kernel<1, 1>, brick_dyn_smem<1>(), e);
         return e;
     }();
     return done;
@@ -205,10 +207,10 @@ unsigned view_chunks(const Grid& G, int chunk) { return (unsigned)((G.nviews + c
 template <int VARIANT, int SCALING>
 void launch_fwd_grid(const kct_plan* p, const Grid& G, int chunk, const float* vol, float* out, int nbatch,
                      cudaStream_t st) {
-    dim3 grid(bricks(G), segments(G), view_chunks(G, chunk) * (unsigned)nbatch);
+    dim3 grid(bricks(G), segments<VARIANT>(G), view_chunks(G, chunk) * (unsigned)nbatch);
     const long long vs = (long long)G.nx * G.ny * G.nz, ps = (long long)G.nu * G.nv * G.nviews;
-    kct::fwd_kernel<VARIANT, SCALING><<<grid, kct::NTHREADS, kBrickDynSmem, st>>>(p->d_views, G, vol, out, vs, ps,
-                                                                                   chunk, p->d_err);
+    kct::fwd_kernel<VARIANT, SCALING><<<grid, kct::NTHREADS, brick_dyn_smem<VARIANT>(), st>>>(
+        p->d_views, G, vol, out, vs, ps, chunk, p->d_err);
 }
 
 template <int VARIANT, int SCALING>
@@ -229,16 +231,16 @@ void launch_fwd_any(const kct_plan* p, const Grid& G, int chunk, const float* vo
 template <int VARIANT, int SCALING>
 void launch_bwd(const kct_plan* p, const float* y, float* vol, int nbatch, int accumulate, cudaStream_t st) {
     const Grid& G = p->grid;
-    dim3 grid(bricks(G), segments(G), (unsigned)nbatch);
+    dim3 grid(bricks(G), segments<VARIANT>(G), (unsigned)nbatch);
     const long long vs = (long long)G.nx * G.ny * G.nz, ps = (long long)G.nu * G.nv * G.nviews;
-    kct::bwd_kernel<VARIANT, SCALING><<<grid, kct::NTHREADS, kBrickDynSmem, st>>>(p->d_views, G, y, vol, vs, ps,
+    kct::bwd_kernel<VARIANT, SCALING><<<grid, kct::NTHREADS, brick_dyn_smem<VARIANT>(), st>>>(p->d_views, G, y, vol, vs, ps,
                                                                                    accumulate, p->d_err);
 }
 
 template <int VARIANT>
 void launch_count(const kct_plan* p, cudaStream_t st) {
     const Grid& G = p->grid;
-    dim3 grid(bricks(G), segments(G), (unsigned)G.nviews);
+    dim3 grid(bricks(G), segments<VARIANT>(G), (unsigned)G.nviews);
     kct::count_kernel<VARIANT><<<grid, kct::NTHREADS, 0, st>>>(p->d_views, G, p->d_count, p->d_err);
 }
 
@@ -789,11 +791,13 @@ extern "C" kct_status kct_project_static(const kct_volume_desc* vol, const kct_d
     e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(S, 0, sizeof(float) * (size_t)npix, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    dim3 grid(bricks(G), segments(G), (unsigned)((G.nviews + kct::VIEW_CHUNK - 1) / kct::VIEW_CHUNK));
+    const unsigned chunks = (unsigned)((G.nviews + kct::VIEW_CHUNK - 1) / kct::VIEW_CHUNK);
     if (variant == KCT_CVP_RELAXED)
-        kct::fwd_kernel<1, -1><<<grid, kct::NTHREADS, kBrickDynSmem, st>>>(d_views, G, d_vol, S, 0, 0, kct::VIEW_CHUNK, d_err);
+        kct::fwd_kernel<1, -1><<<dim3(bricks(G), segments<1>(G), chunks), kct::NTHREADS, brick_dyn_smem<1>(), st>>>(
+            d_views, G, d_vol, S, 0, 0, kct::VIEW_CHUNK, d_err);
     else
-        kct::fwd_kernel<0, -1><<<grid, kct::NTHREADS, kBrickDynSmem, st>>>(d_views, G, d_vol, S, 0, 0, kct::VIEW_CHUNK, d_err);
+        kct::fwd_kernel<0, -1><<<dim3(bricks(G), segments<0>(G), chunks), kct::NTHREADS, brick_dyn_smem<0>(), st>>>(
+            d_views, G, d_vol, S, 0, 0, kct::VIEW_CHUNK, d_err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "forward projection launch");
     dim3 sgrid((unsigned)(((long)G.nu * G.nv + 255) / 256), G.nviews);
