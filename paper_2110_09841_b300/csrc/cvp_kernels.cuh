@@ -432,28 +432,43 @@ __device__ __noinline__ void build_column_cut(const View* Vp, const Column* Cp, 
     float* px = ws->px[c];
     const int nv = clip_square(V, lo, hi, pt, px);
     ws->nv[c] = nv;
-    const Mom f = normalise(polygon_cut<true>(pt, px, nv, 3.0e38f), C.tc, C.xc);
-    float tlo = 3.0e38f, thi = -3.0e38f;
-    for (int q = 0; q < nv; ++q) { tlo = fminf(tlo, pt[q]); thi = fmaxf(thi, pt[q]); }
     if (variant == 1) {
-        const float tn = C.tc + (f.m1 > 0.f ? f.mt / f.m1 : 0.f);
-        const float itn = 1.0f / tn;
-        ws->fa[c] = make_float4(f.m1, tn, itn, 0.5f * az * fabsf(V.gv) * itn);
-    } else {
-        ws->fa[c] = make_float4(f.m1, f.mt, f.mtt, f.ml);
-        ws->fb[c] = make_float4(f.mlt, tlo, thi, 0.f);
-        ws->fr[c] = make_float2(1.0f / (C.tc + tlo), 1.0f / (C.tc + thi));
+        // area and depth centroid only
+        Mom5 g = mom_zero();
         for (int e = 0; e < nv; ++e) {
-            const int g = (e + 1 == nv) ? 0 : e + 1;
-            Mom5 m = mom_zero();
-            seg_acc<true>(m, pt[e], px[e], pt[g], px[g]);
-            ws->eg[c][e][0] = m.a;
-            ws->eg[c][e][1] = m.t;
-            ws->eg[c][e][2] = m.x;
-            ws->eg[c][e][3] = m.tt;
-            ws->eg[c][e][4] = m.tx;
+            const int f = (e + 1 == nv) ? 0 : e + 1;
+            seg_acc<false>(g, pt[e], px[e], pt[f], px[f]);
         }
+        const float m1 = 0.5f * g.a, mt = g.t * (1.f / 6.f);
+        const float tn = C.tc + (m1 > 0.f ? mt / m1 : 0.f);
+        const float itn = 1.0f / tn;
+        ws->fa[c] = make_float4(m1, tn, itn, 0.5f * az * fabsf(V.gv) * itn);
+        return;
     }
+    // Green terms of each edge (kept for the cuts at crossing depths) and their sum
+    Mom5 g = mom_zero();
+    float tlo = 3.0e38f, thi = -3.0e38f;
+    for (int e = 0; e < nv; ++e) {
+        const int f = (e + 1 == nv) ? 0 : e + 1;
+        Mom5 m = mom_zero();
+        seg_acc<true>(m, pt[e], px[e], pt[f], px[f]);
+        ws->eg[c][e][0] = m.a;
+        ws->eg[c][e][1] = m.t;
+        ws->eg[c][e][2] = m.x;
+        ws->eg[c][e][3] = m.tt;
+        ws->eg[c][e][4] = m.tx;
+        g.a += m.a;
+        g.t += m.t;
+        g.x += m.x;
+        g.tt += m.tt;
+        g.tx += m.tx;
+        tlo = fminf(tlo, pt[e]);
+        thi = fmaxf(thi, pt[e]);
+    }
+    const Mom f = normalise(g, C.tc, C.xc);
+    ws->fa[c] = make_float4(f.m1, f.mt, f.mtt, f.ml);
+    ws->fb[c] = make_float4(f.mlt, tlo, thi, 0.f);
+    ws->fr[c] = make_float2(1.0f / (C.tc + tlo), 1.0f / (C.tc + thi));
 }
 
 // All pairs of voxels kbase .. kbase + runs * SEG - 1 of column (i, j) in view V (in shared
