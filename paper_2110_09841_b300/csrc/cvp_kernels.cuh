@@ -23,6 +23,8 @@
 // <A x, y> = <x, A^T y> holds to float rounding.
 #pragma once
 
+#include <type_traits>
+
 #include "cvp_device.cuh"
 
 namespace kct {
@@ -38,16 +40,16 @@ constexpr int NTHREADS = 32 * NWARP;
 // Brick::DYN_FLOATS floats) is sized accordingly.
 constexpr int EV_CAP = 64;         // crossing events queued per warp and round (>= KPL * KCT_ROWS)
 constexpr int KCT_ROWS = 32;       // row boundaries of one voxel (its footprint spans <= 31 rows)
-constexpr int TILE_CAP = 7168;     // floats of the shared detector tile (relaxed kernels)
 
-// Brick height along x_3 per variant: the near-exact kernels take two runs of SEG voxels per
-// column-cut build (the build is about a fifth of their time), the relaxed ones one run (so
-// that three of their blocks fit on an SM).
-template <int VARIANT>
+// Brick height along x_3: two runs of SEG voxels per column-cut build (the build is a large
+// part of the per-voxel work), except for the relaxed adjoint (one run: measured faster).
+// Detector tile: 12288 floats for the near-exact kernels (2 blocks per SM), 8192 for the
+// relaxed ones (3 blocks per SM, small static shared memory).
+template <int VARIANT, bool FWD = true>
 struct Brick {
-    static constexpr int RUNS = VARIANT == 0 ? 2 : 1;
+    static constexpr int RUNS = (VARIANT == 0 || FWD) ? 2 : 1;  // relaxed adjoint: measured faster with 1
     static constexpr int Z = SEG * RUNS;                       // voxels along x_3
-    static constexpr int TILE = VARIANT == 0 ? 12288 : TILE_CAP;   // floats of the detector tile
+    static constexpr int TILE = VARIANT == 0 ? 12288 : 8192;   // floats of the detector tile
     static constexpr int DYN_FLOATS = Z * NCOLS + TILE;        // dynamic shared memory
 };
 constexpr int VIEW_CHUNK = 16;     // default views per forward block (a plan may tune it)
@@ -67,15 +69,26 @@ struct WarpSmem {
     float res_v[EV_CAP], res_q[EV_CAP];
 };
 
+// The relaxed kernels keep only the column cuts' areas and depth centroids, so that their
+// blocks stay small.
+struct WarpSmemRelaxed {
+    Column C;
+    float4 fa[KCT_CB];             // A_n, t_n, 1/t_n, half the voxel's projected row extent
+};
+
 struct Tile {                      // detector window covered by a brick in one view
     int u0, v0, w, h, ok;
 };
 
-struct BlockSmem {
+template <class WS>
+struct BlockSmemOf {
     View V;
     Tile T;
-    WarpSmem ws[NWARP];
+    WS ws[NWARP];
 };
+
+template <int VARIANT>
+using BlockSmem = BlockSmemOf<typename std::conditional<VARIANT == 0, WarpSmem, WarpSmemRelaxed>::type>;
 
 // Row-boundary classes (in the sense of the region v < V_b)
 enum { ROW_ZERO = 0, ROW_FULL = 1, ROW_LIN = 2, ROW_CROSS = 3 };
@@ -391,7 +404,8 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
 // the overlap is evaluated relative to v_n so that no large row index enters a difference.
 template <class Sink>
 __device__ __forceinline__ void relaxed_voxels(const View& V, const Grid& G, const Column& C, int cstart, int ncol,
-                                               int kbase, int lane, WarpSmem* ws, Sink& sink, int* err) {
+                                               int kbase, int lane, const WarpSmemRelaxed* ws, Sink& sink,
+                                               int* err) {
     const float az = G.az;
     for (int pass = 0; pass < KPL; ++pass) {
         const int k = kbase + pass * 32 + lane;
@@ -420,10 +434,31 @@ __device__ __forceinline__ void relaxed_voxels(const View& V, const Grid& G, con
     }
 }
 
-// H_n for detector column n: its vertices, moments and depth range into ws slot c.
+// H_n for detector column n, relaxed variant: its area and depth centroid into slot c.
 // Not inlined: it runs once per column and view.
-__device__ __noinline__ void build_column_cut(const View* Vp, const Column* Cp, float az, int n, int variant,
-                                              WarpSmem* ws, int c) {
+__device__ __noinline__ void build_column_cut(const View* Vp, const Column* Cp, float az, int n,
+                                              WarpSmemRelaxed* ws, int c) {
+    const View& V = *Vp;
+    const Column& C = *Cp;
+    Line lo, hi;
+    column_lines(V, C, n, lo, hi);
+    float pt[8], px[8];
+    const int nv = clip_square(V, lo, hi, pt, px);
+    Mom5 g = mom_zero();
+    for (int e = 0; e < nv; ++e) {
+        const int f = (e + 1 == nv) ? 0 : e + 1;
+        seg_acc<false>(g, pt[e], px[e], pt[f], px[f]);
+    }
+    const float m1 = 0.5f * g.a, mt = g.t * (1.f / 6.f);
+    const float tn = C.tc + (m1 > 0.f ? mt / m1 : 0.f);
+    const float itn = 1.0f / tn;
+    ws->fa[c] = make_float4(m1, tn, itn, 0.5f * az * fabsf(V.gv) * itn);
+}
+
+// H_n for detector column n, near-exact variant: its vertices, the Green terms of its edges,
+// its moments and depth range into slot c. Not inlined: it runs once per column and view.
+__device__ __noinline__ void build_column_cut(const View* Vp, const Column* Cp, float az, int n, WarpSmem* ws,
+                                              int c) {
     const View& V = *Vp;
     const Column& C = *Cp;
     Line lo, hi;
@@ -432,19 +467,6 @@ __device__ __noinline__ void build_column_cut(const View* Vp, const Column* Cp, 
     float* px = ws->px[c];
     const int nv = clip_square(V, lo, hi, pt, px);
     ws->nv[c] = nv;
-    if (variant == 1) {
-        // area and depth centroid only
-        Mom5 g = mom_zero();
-        for (int e = 0; e < nv; ++e) {
-            const int f = (e + 1 == nv) ? 0 : e + 1;
-            seg_acc<false>(g, pt[e], px[e], pt[f], px[f]);
-        }
-        const float m1 = 0.5f * g.a, mt = g.t * (1.f / 6.f);
-        const float tn = C.tc + (m1 > 0.f ? mt / m1 : 0.f);
-        const float itn = 1.0f / tn;
-        ws->fa[c] = make_float4(m1, tn, itn, 0.5f * az * fabsf(V.gv) * itn);
-        return;
-    }
     // Green terms of each edge (kept for the cuts at crossing depths) and their sum
     Mom5 g = mom_zero();
     float tlo = 3.0e38f, thi = -3.0e38f;
@@ -474,9 +496,9 @@ __device__ __noinline__ void build_column_cut(const View* Vp, const Column* Cp, 
 // All pairs of voxels kbase .. kbase + runs * SEG - 1 of column (i, j) in view V (in shared
 // memory): each column cut is built once and used by `runs` runs of SEG voxels; the sink is
 // told when a run ends. Called by all 32 lanes of a warp with the same arguments.
-template <int VARIANT, class Sink>
+template <int VARIANT, class Sink, class WS>
 __device__ __forceinline__ void warp_column(const View& V, const Grid& G, int i, int j, int kbase, int runs,
-                                            int lane, WarpSmem* ws, Sink& sink, int* err) {
+                                            int lane, WS* ws, Sink& sink, int* err) {
     Column C;
     if (!column_setup(V, G, i, j, C)) return;
     if (C.n_last - C.n_first + 2 > KCT_MAX_SPAN) {
@@ -486,13 +508,13 @@ __device__ __forceinline__ void warp_column(const View& V, const Grid& G, int i,
     for (int cstart = C.n_first; cstart <= C.n_last; cstart += KCT_CB) {
         const int ncol = min(KCT_CB, C.n_last - cstart + 1);
         __syncwarp();              // the previous readers of ws are done
-        if (lane < ncol) build_column_cut(&V, &C, G.az, cstart + lane, VARIANT, ws, lane);
+        if (lane < ncol) build_column_cut(&V, &C, G.az, cstart + lane, ws, lane);
         __syncwarp();
 #pragma unroll 1
         for (int r = 0; r < runs; ++r) {
             const int kb = kbase + r * SEG;
             if (kb >= G.nz) break;
-            if (VARIANT == 1) relaxed_voxels(V, G, C, cstart, ncol, kb, lane, ws, sink, err);
+            if constexpr (VARIANT == 1) relaxed_voxels(V, G, C, cstart, ncol, kb, lane, ws, sink, err);
             else exact_voxels(V, G, C, cstart, ncol, kb, lane, ws, sink, err);
             sink.end_run(r);
         }
@@ -633,7 +655,7 @@ __global__ void __launch_bounds__(NTHREADS, VARIANT == 1 ? 3 : 2) fwd_kernel(con
                                                           long long vstride, long long pstride, int view_chunk,
                                                           int* err) {
     extern __shared__ float dyn[];
-    __shared__ BlockSmem bs;
+    __shared__ BlockSmem<VARIANT> bs;
     using B = Brick<VARIANT>;
     float* mu_s = dyn;
     float* tile = dyn + B::Z * NCOLS;
@@ -690,8 +712,8 @@ __global__ void __launch_bounds__(NTHREADS, VARIANT == 1 ? 3 : 2) bwd_kernel(con
                                                           long long vstride, long long pstride, int accumulate,
                                                           int* err) {
     extern __shared__ float dyn[];
-    __shared__ BlockSmem bs;
-    using B = Brick<VARIANT>;
+    __shared__ BlockSmem<VARIANT> bs;
+    using B = Brick<VARIANT, false>;
     float* acc_s = dyn;                 // [NCOLS][B::Z]
     float* tile = dyn + B::Z * NCOLS;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -740,7 +762,7 @@ __global__ void __launch_bounds__(NTHREADS, VARIANT == 1 ? 3 : 2) bwd_kernel(con
 template <int VARIANT>
 __global__ void __launch_bounds__(NTHREADS, 2) count_kernel(const View* __restrict__ views, Grid G,
                                                             unsigned long long* count, int* err) {
-    __shared__ BlockSmem bs;
+    __shared__ BlockSmem<VARIANT> bs;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int i0, j0;
     brick_origin(G, i0, j0);

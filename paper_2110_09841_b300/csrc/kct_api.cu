@@ -170,11 +170,13 @@ unsigned bricks(const Grid& G) {
     return (unsigned)(((G.nx + kct::BX - 1) / kct::BX) * ((G.ny + kct::BY - 1) / kct::BY));
 }
 
-template <int VARIANT>
-unsigned segments(const Grid& G) { return (unsigned)((G.nz + kct::Brick<VARIANT>::Z - 1) / kct::Brick<VARIANT>::Z); }
+template <int VARIANT, bool FWD = true>
+unsigned segments(const Grid& G) {
+    return (unsigned)((G.nz + kct::Brick<VARIANT, FWD>::Z - 1) / kct::Brick<VARIANT, FWD>::Z);
+}
 
-template <int VARIANT>
-constexpr size_t brick_dyn_smem() { return sizeof(float) * kct::Brick<VARIANT>::DYN_FLOATS; }
+template <int VARIANT, bool FWD = true>
+constexpr size_t brick_dyn_smem() { return sizeof(float) * kct::Brick<VARIANT, FWD>::DYN_FLOATS; }
 
 // opt in to more than 48 KB of shared memory per block (once per process)
 template <class K>
@@ -191,10 +193,10 @@ cudaError_t brick_kernel_attributes() {
         e = set_dyn(kct::fwd_kernel<1, 1>, brick_dyn_smem<1>(), e);
         e = set_dyn(kct::fwd_kernel<0, -1>, brick_dyn_smem<0>(), e);
         e = set_dyn(kct::fwd_kernel<1, -1>, brick_dyn_smem<1>(), e);
-        e = set_dyn(kct::bwd_kernel<0, 0>, brick_dyn_smem<0>(), e);
-        e = set_dyn(kct::bwd_kernel<0, 1>, brick_dyn_smem<0>(), e);
-        e = set_dyn(kct::bwd_kernel<1, 0>, brick_dyn_smem<1>(), e);
-        e = set_dyn(kct::bwd_kernel<1, 1>, brick_dyn_smem<1>(), e);
+        e = set_dyn(kct::bwd_kernel<0, 0>, brick_dyn_smem<0, false>(), e);
+        e = set_dyn(kct::bwd_kernel<0, 1>, brick_dyn_smem<0, false>(), e);
+        e = set_dyn(kct::bwd_kernel<1, 0>, brick_dyn_smem<1, false>(), e);
+        e = set_dyn(kct::bwd_kernel<1, 1>, brick_dyn_smem<1, false>(), e);
         return e;
     }();
     return done;
@@ -231,9 +233,9 @@ void launch_fwd_any(const kct_plan* p, const Grid& G, int chunk, const float* vo
 template <int VARIANT, int SCALING>
 void launch_bwd(const kct_plan* p, const float* y, float* vol, int nbatch, int accumulate, cudaStream_t st) {
     const Grid& G = p->grid;
-    dim3 grid(bricks(G), segments<VARIANT>(G), (unsigned)nbatch);
+    dim3 grid(bricks(G), segments<VARIANT, false>(G), (unsigned)nbatch);
     const long long vs = (long long)G.nx * G.ny * G.nz, ps = (long long)G.nu * G.nv * G.nviews;
-    kct::bwd_kernel<VARIANT, SCALING><<<grid, kct::NTHREADS, brick_dyn_smem<VARIANT>(), st>>>(p->d_views, G, y, vol, vs, ps,
+    kct::bwd_kernel<VARIANT, SCALING><<<grid, kct::NTHREADS, brick_dyn_smem<VARIANT, false>(), st>>>(p->d_views, G, y, vol, vs, ps,
                                                                                    accumulate, p->d_err);
 }
 
