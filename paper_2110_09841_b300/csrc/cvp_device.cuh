@@ -166,58 +166,6 @@ KCT_HD Line line_none() { return Line{0.f, 0.f, 1.f}; }
 
 KCT_HD float line_eval(const Line& l, float t, float x) { return fmaf(l.at, t, fmaf(l.ax, x, -l.c)); }
 
-// Green sums of  square ∩ H0 ∩ H1 ∩ H2  for three half-planes (any of them inactive).
-// The boundary of an intersection of convex sets is the union of each set's boundary
-// restricted to the others: the square's edges clipped by the three half-planes, plus, for
-// each line, its chord through the square (from the point where the counter-clockwise
-// boundary leaves the half-plane to where it re-enters) clipped by the other two.
-template <bool FULL>
-KCT_HD Mom5 region3(const View& V, const Line& l0, const Line& l1, const Line& l2) {
-    Mom5 m = mom_zero();
-    float L[3][4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        L[0][e] = line_eval(l0, V.sq_t[e], V.sq_x[e]);
-        L[1][e] = line_eval(l1, V.sq_t[e], V.sq_x[e]);
-        L[2][e] = line_eval(l2, V.sq_t[e], V.sq_x[e]);
-    }
-    float xt[3], xx[3], nt[3], nx[3];   // exit and entry points of each line's chord
-    bool hx[3], hn[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) { xt[k] = xx[k] = nt[k] = nx[k] = 0.f; hx[k] = hn[k] = false; }
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        const int f = (e + 1) & 3;
-        const float pt = V.sq_t[e], px = V.sq_x[e], qt = V.sq_t[f], qx = V.sq_x[f];
-        float s0 = 0.f, s1 = 1.f;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) clip_param(L[k][e], L[k][f], s0, s1);
-        seg_part<FULL>(m, pt, px, qt, qx, s0, s1);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            if ((L[k][e] < 0.f) != (L[k][f] < 0.f)) {
-                float ss = L[k][e] / (L[k][e] - L[k][f]);
-                float ct = fmaf(ss, qt - pt, pt), cx = fmaf(ss, qx - px, px);
-                if (L[k][e] < 0.f) { xt[k] = ct; xx[k] = cx; hx[k] = true; }
-                else { nt[k] = ct; nx[k] = cx; hn[k] = true; }
-            }
-        }
-    }
-    const Line* ls[3] = {&l0, &l1, &l2};
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        if (hx[k] && hn[k]) {
-            float s0 = 0.f, s1 = 1.f;
-#pragma unroll
-            for (int q = 0; q < 3; ++q)
-                if (q != k)
-                    clip_param(line_eval(*ls[q], xt[k], xx[k]), line_eval(*ls[q], nt[k], nx[k]), s0, s1);
-            seg_part<FULL>(m, xt[k], xx[k], nt[k], nx[k], s0, s1);
-        }
-    }
-    return m;
-}
-
 // Vertices (counter-clockwise) of the square clipped by two half-planes: each square edge
 // contributes its start vertex when inside both, then, in order along the edge, the points
 // where it crosses a line while inside the other half-plane. At most 8 points.
@@ -251,31 +199,6 @@ KCT_HD int clip_square(const View& V, const Line& l0, const Line& l1, float* pt,
         }
     }
     return nv;
-}
-
-// Green sums of  polygon ∩ {t' < tau}  for a convex polygon given by its vertices: the edges
-// clipped to the half-plane plus the chord along t' = tau from the exit to the entry point.
-template <bool FULL>
-KCT_HD Mom5 polygon_cut(const float* pt, const float* px, int nv, float tau) {
-    Mom5 m = mom_zero();
-    float xt = 0.f, xx = 0.f, nt = 0.f, nx = 0.f;
-    bool hx = false, hn = false;
-    for (int e = 0; e < nv; ++e) {
-        const int f = (e + 1 == nv) ? 0 : e + 1;
-        const float at = pt[e], ax = px[e], bt = pt[f], bx = px[f];
-        const float La = at - tau, Lb = bt - tau;
-        float s0 = 0.f, s1 = 1.f;
-        clip_param(La, Lb, s0, s1);
-        seg_part<FULL>(m, at, ax, bt, bx, s0, s1);
-        if ((La < 0.f) != (Lb < 0.f)) {
-            const float ss = La / (La - Lb);
-            const float ct = fmaf(ss, bt - at, at), cx = fmaf(ss, bx - ax, ax);
-            if (La < 0.f) { xt = ct; xx = cx; hx = true; }
-            else { nt = ct; nx = cx; hn = true; }
-        }
-    }
-    if (hx && hn) seg_acc<FULL>(m, xt, xx, nt, nx);
-    return m;
 }
 
 // ----------------------------------------------------------------------------------------
@@ -319,43 +242,6 @@ KCT_HD bool column_setup(const View& V, const Grid& G, int i, int j, Column& C) 
     return C.n_first <= C.n_last;
 }
 
-// Voxel k of the column: height zeta_c of its centre, projected centre beta_c, row range.
-struct Slice {
-    float zc;            // zeta of the voxel centre
-    float bc;            // zeta_c / t_c
-    float vmin, vmax;
-    int m_first, m_last;
-};
-
-KCT_HD bool slice_setup(const View& V, const Grid& G, const Column& C, int k, Slice& S) {
-    float z = fmaf((float)k, G.az, G.z0);
-    float zc = z - V.sz;
-    S.zc = zc;
-    S.bc = zc * C.itc;
-    float it0 = 1.0f / (C.tc + V.tmin_sq), it1 = 1.0f / (C.tc + V.tmax_sq);
-    float zl = zc - 0.5f * G.az, zh = zc + 0.5f * G.az;
-    float b00 = zl * it0, b01 = zl * it1, b10 = zh * it0, b11 = zh * it1;
-    float bmin = fminf(fminf(b00, b01), fminf(b10, b11));
-    float bmax = fmaxf(fmaxf(b00, b01), fmaxf(b10, b11));
-    float va = fmaf(V.gv, bmin, V.cv), vb = fmaf(V.gv, bmax, V.cv);
-    S.vmin = fminf(va, vb);
-    S.vmax = fmaxf(va, vb);
-    int m0 = (int)floorf(S.vmin + 0.5f), m1 = (int)floorf(S.vmax + 0.5f);
-    S.m_first = max(m0, 0);
-    S.m_last = min(m1, G.nv - 1);
-    return S.m_first <= S.m_last;
-}
-
-// Row boundary V in the voxel: h(t') = clamp(p0 + p1 t', 0, az) is the height of the part
-// of the column above base point t' that projects to v < V.
-KCT_HD void row_plane(const View& V, const Grid& G, const Column& C, const Slice& S,
-                                          float Vb, float& p0, float& p1) {
-    // V - v_c with v_c = cv + gv beta_c, evaluated as one fused operation
-    float dv = -fmaf(V.gv, S.bc, V.cv - Vb);
-    p0 = fmaf(C.tc * dv, V.inv_agv, 0.5f * G.az);
-    p1 = (Vb - V.cv) * V.inv_agv;
-}
-
 // ----------------------------------------------------------------------------------------
 // Column cuts and their moments
 // ----------------------------------------------------------------------------------------
@@ -390,14 +276,6 @@ KCT_HD void column_lines(const View& V, const Column& C, int n, Line& lo, Line& 
     else lo = line_none();
     if (Uh < C.umax) hi = Line{(V.cu - Uh) * C.itc, C.gxi, -fmaf(V.gu, C.alc, V.cu - Uh)};
     else hi = line_none();
-}
-
-// moments over H_n ∩ {t' < tau}
-KCT_HD Mom cut_moments(const View& V, const Column& C, const Line& lo, const Line& hi,
-                                           const Mom& full, float tau) {
-    if (tau <= V.tmin_sq) return Mom{0.f, 0.f, 0.f, 0.f, 0.f};
-    if (tau >= V.tmax_sq) return full;
-    return normalise(region3<true>(V, lo, hi, Line{1.f, 0.f, tau}), C.tc, C.xc);
 }
 
 }  // namespace kct

@@ -90,38 +90,10 @@ struct BlockSmemOf {
 template <int VARIANT>
 using BlockSmem = BlockSmemOf<typename std::conditional<VARIANT == 0, WarpSmem, WarpSmemRelaxed>::type>;
 
-// Row-boundary classes (in the sense of the region v < V_b)
-enum { ROW_ZERO = 0, ROW_FULL = 1, ROW_LIN = 2, ROW_CROSS = 3 };
-
-// Height of {v < V_b} over base point t' is clamp(p0 + p1 t', 0, az), measured from the face
-// on which that region sits ("bottom frame"). The complementary region {v > V_b} has height
-// clamp(pt0 - p1 t', 0, az), pt0 = az - p0, measured from the opposite face ("top frame").
-struct RowPlane {
-    int cls;
-    float p0, p1, pt0;
-};
-
-KCT_HD RowPlane row_boundary(const View& V, const Grid& G, const Column& C, const Slice& S, float Vb) {
-    RowPlane r;
-    r.p0 = r.p1 = 0.f;
-    r.pt0 = G.az;
-    if (Vb <= S.vmin) { r.cls = ROW_ZERO; return r; }
-    if (Vb >= S.vmax) { r.cls = ROW_FULL; r.p0 = G.az; r.pt0 = 0.f; return r; }
-    const float dv = -fmaf(V.gv, S.bc, V.cv - Vb);        // V_b - v_c
-    const float off = C.tc * dv * V.inv_agv;
-    r.p0 = 0.5f * G.az + off;
-    r.pt0 = 0.5f * G.az - off;
-    r.p1 = (Vb - V.cv) * V.inv_agv;
-    // does the plane leave the voxel through a horizontal face inside the base's depth range?
-    const float h_lo = fmaf(r.p1, V.tmin_sq, r.p0), h_hi = fmaf(r.p1, V.tmax_sq, r.p0);
-    r.cls = (fminf(h_lo, h_hi) < 0.f || fmaxf(h_lo, h_hi) > G.az) ? ROW_CROSS : ROW_LIN;
-    return r;
-}
-
 // Moments (1, t', t'^2, lambda, lambda t') of H_n ∩ {t' < tau} from the vertices of H_n:
 // Green's theorem over the boundary of the cut, i.e. the edges below tau (their whole-edge
 // terms are precomputed in eg), the clipped parts of the two edges that cross t' = tau, and
-// the chord along t' = tau. Same sums in the same order as polygon_cut.
+// the chord along t' = tau.
 // Not inlined: the clipping exists once in the code and its callers stay small.
 __device__ __noinline__ Mom cut_moments_call(const float* pt, const float* px, const float (*eg)[5], int nv,
                                              float tau, float tc, float xc) {
