@@ -40,14 +40,14 @@ UNIT = "Gvoxel·views/s"
 # volume once per chunk of 16 views and adds one projection per view, the adjoint reads one
 # projection tile per view and writes the volume once, so traffic is scaled as below.
 NCU = {
-    "exact project": {"flop_per_vv": 1015.2, "warp_per_vv": 125.3, "simt": 0.56,
-                      "dram_read_8": 5.7995e8, "dram_write_8": 3.3333e7},
-    "exact backproject": {"flop_per_vv": 1077.4, "warp_per_vv": 129.2, "simt": 0.57,
-                          "dram_read_8": 5.6781e7, "dram_write_8": 4.9357e8},
-    "relaxed project": {"flop_per_vv": 168.9, "warp_per_vv": 31.0, "simt": 0.55,
-                        "dram_read_8": 5.7136e8, "dram_write_8": 3.1922e7},
-    "relaxed backproject": {"flop_per_vv": 201.0, "warp_per_vv": 35.1, "simt": 0.57,
-                            "dram_read_8": 4.8661e7, "dram_write_8": 4.8807e8},
+    "exact project": {"flop_per_vv": 978.7, "warp_per_vv": 113.3, "simt": 0.59,
+                      "dram_read_8": 5.7855e8, "dram_write_8": 3.0845e7},
+    "exact backproject": {"flop_per_vv": 1049.1, "warp_per_vv": 118.1, "simt": 0.61,
+                          "dram_read_8": 5.9906e7, "dram_write_8": 4.9308e8},
+    "relaxed project": {"flop_per_vv": 159.0, "warp_per_vv": 25.2, "simt": 0.64,
+                        "dram_read_8": 5.7645e8, "dram_write_8": 3.1410e7},
+    "relaxed backproject": {"flop_per_vv": 196.0, "warp_per_vv": 35.0, "simt": 0.60,
+                            "dram_read_8": 5.2890e7, "dram_write_8": 4.9617e8},
 }
 
 
