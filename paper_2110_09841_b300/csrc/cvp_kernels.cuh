@@ -318,12 +318,17 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
                     const int rb = (R[p] + 1) >> 1;
                     const unsigned mbot = cross[p] & ((2u << rb) - 1u), mtop = cross[p] & ~((1u << rb) - 1u);
                     const int nbot = __popc(mbot);
+                    // region value of the previous row's upper plane, reused as this row's lower
+                    // plane when both rows use the same frame
+                    float carry_v = 0.f, carry_q = 0.f;
+                    bool carry = false;
 #pragma unroll 1
                     for (int r = 0; r < R[p]; ++r) {
                         const int m = m_first[p] + r;
                         const unsigned bl = 1u << r, bh = 2u << r;
                         float pv, pq;
                         if (!((cross[p] | zero[p] | full[p]) & (bl | bh))) {
+                            carry = false;
                             // both planes inside: height dp0 + dp1 t' centred at s0 + s1 t'
                             const float s0 = C.tc * (-fmaf(V.gv, bc, V.cv - (float)m)) * V.inv_agv;
                             const float s1 = ((float)m - V.cv) * V.inv_agv;
@@ -333,8 +338,12 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
                         } else {
                             const bool top = r >= rb;
                             float g[2][2];
+                            const bool reuse = carry && r != rb;
+                            g[0][0] = carry_v;
+                            g[0][1] = carry_q;
 #pragma unroll
                             for (int h = 0; h < 2; ++h) {
+                                if (h == 0 && reuse) continue;
                                 const int b = r + h;
                                 const unsigned bit = 1u << b;
                                 float p0 = fmaf(0.5f, az, fmaf((float)b, dp0, off0)), p1 = fmaf((float)b, dp1, p1_0);
@@ -352,6 +361,9 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
                             }
                             pv = top ? g[0][0] - g[1][0] : g[1][0] - g[0][0];
                             pq = top ? g[0][1] - g[1][1] : g[1][1] - g[0][1];
+                            carry_v = g[1][0];
+                            carry_q = g[1][1];
+                            carry = true;
                         }
                         if (pv > vtiny) sink.pair(p, n, m, pair_weight(pv, pq, D2));
                     }
