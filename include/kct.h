@@ -63,7 +63,7 @@ typedef enum kct_status {
     KCT_ERR_CUDA = 3,          /* a CUDA runtime call or kernel launch failed */
     KCT_ERR_OOM = 4,           /* device or host allocation failed in kct_plan_create */
     KCT_ERR_DEVICE_CHECK = 5,  /* a kernel reported an inconsistent footprint */
-    KCT_ERR_UNSUPPORTED = 6    /* request outside what this build supports */
+    KCT_ERR_UNSUPPORTED = 6    /* request outside what the library supports */
 } kct_status;
 
 typedef enum kct_variant {

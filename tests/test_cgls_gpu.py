@@ -61,7 +61,7 @@ def test_iterates_match_oracle(vname, variant, gname):
 
 
 @pytest.mark.parametrize("vname,variant", [("exact", oracle.EXACT), ("relaxed", oracle.RELAXED)])
-def test_reaches_tolerance_judged_by_oracle(vname, variant):
+def test_reaches_tolerance_checked_by_oracle(vname, variant):
     g = small()
     b = oracle.project(g, phantom(g, 5), variant)
     A = Projector(g, vname, "cos")
