@@ -40,14 +40,14 @@ UNIT = "Gvoxel·views/s"
 # volume once per chunk of 16 views and adds one projection per view, the adjoint reads one
 # projection tile per view and writes the volume once, so traffic is scaled as below.
 NCU = {
-    "exact project": {"flop_per_vv": 978.7, "warp_per_vv": 113.3, "simt": 0.59,
-                      "dram_read_8": 5.7855e8, "dram_write_8": 3.0845e7},
-    "exact backproject": {"flop_per_vv": 1049.1, "warp_per_vv": 118.1, "simt": 0.61,
-                          "dram_read_8": 5.9906e7, "dram_write_8": 4.9308e8},
+    "exact project": {"flop_per_vv": 964.4, "warp_per_vv": 112.4, "simt": 0.61,
+                      "dram_read_8": 5.7736e8, "dram_write_8": 3.0488e7},
+    "exact backproject": {"flop_per_vv": 1034.8, "warp_per_vv": 117.3, "simt": 0.62,
+                          "dram_read_8": 5.9742e7, "dram_write_8": 4.9289e8},
     "relaxed project": {"flop_per_vv": 159.0, "warp_per_vv": 25.2, "simt": 0.64,
-                        "dram_read_8": 5.7645e8, "dram_write_8": 3.1410e7},
+                        "dram_read_8": 5.7725e8, "dram_write_8": 3.1695e7},
     "relaxed backproject": {"flop_per_vv": 196.0, "warp_per_vv": 35.0, "simt": 0.60,
-                            "dram_read_8": 5.2890e7, "dram_write_8": 4.9617e8},
+                            "dram_read_8": 5.6709e7, "dram_write_8": 4.9702e8},
 }
 
 
