@@ -59,7 +59,12 @@ def full_launch_traffic(name: str, nviews: int) -> float:
     return c["dram_read_8"] * chunks + c["dram_write_8"] * nviews / 8
 
 
-def parse():
+def default_args():
+    """The arguments of a run without command-line options."""
+    return parse([])
+
+
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -81,7 +86,7 @@ def parse():
     ap.add_argument("--variant", default="exact", choices=["exact", "relaxed"])
     ap.add_argument("--direction", default="fwd", choices=["fwd", "bwd"])
     ap.add_argument("--views", type=int, default=32)
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def run_profile_case(args):

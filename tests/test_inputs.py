@@ -52,3 +52,33 @@ def test_phantom_is_seeded_and_additive():
     g = inputs.workload_geometry("cvp32")
     one = [inputs.voxelize(g, [e]).numpy() for e in ells]
     np.testing.assert_allclose(sum(one), a, atol=1e-7)
+
+
+def test_poisson_log_data_statistics():
+    """b = -ln(max(N, 1) / I0), N ~ Poisson(I0 exp(-clean)): mean close to the clean line
+    integral, variance close to exp(clean) / I0 (delta method), seeded."""
+    import torch
+
+    clean = torch.full((200000,), 0.8)
+    b = inputs.poisson_log_data(clean, 1e5, 11)
+    assert torch.equal(b, inputs.poisson_log_data(clean, 1e5, 11))
+    assert abs(float(b.mean()) - 0.8) < 1e-4
+    var = float(b.double().var())
+    assert abs(var / (math.exp(0.8) / 1e5) - 1.0) < 0.02
+    # no photons counted: clamped to one count
+    assert float(inputs.poisson_log_data(torch.full((4,), 60.0), 1e5, 1).max()) == pytest.approx(math.log(1e5), rel=1e-6)
+
+
+def test_perfusion_frames_follow_bolus_curves():
+    """Frames differ only inside the vessel ellipsoids; the static background is shared."""
+    g = inputs.make_geometry((24, 24, 20), (1.0, 1.0, 1.0), (48, 40), (0.8, 0.8), 4, 750.0, 1200.0, 360.0)
+    f = inputs.perfusion_frames(g, 31, frames=6)
+    assert f.shape == (6,) + g.vol_shape
+    d = (f - f[0]).abs().amax(dim=0)
+    assert 0 < int((d > 0).sum()) < d.numel() // 2
+    assert bool((f >= 0).all())
+
+
+def test_cgls_workload_shapes():
+    g = inputs.workload_geometry("cgls128")
+    assert g.vol_shape == (128, 128, 128) and g.proj_shape == (180, 192, 256)
