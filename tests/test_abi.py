@@ -87,6 +87,8 @@ def test_rejects_invalid_arguments(lib):
     assert lib.kct_plan_autotune(None, None, None, None, None, None) == 1
     assert lib.kct_cgls_workspace_bytes(None) == 0
     assert lib.kct_cgls(None, None, None, 0, 1, 1e-3, None, 0, None, None, None, None) == 1
+    assert lib.kct_siddon_project(None, None, None, 8, 0, None) == 1
+    assert lib.kct_plan_get_view_chunk(None, None) == 1
 
 
 def test_rejects_geometry_outside_the_arrangement(lib):
