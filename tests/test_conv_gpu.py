@@ -119,3 +119,43 @@ def test_autograd_function_gradients():
     check(x.grad, to_cf_inv(rx), to_cf_inv(ax), 2.0 ** -8)
     check(wt.grad, rw.reshape(co, ci, 27).permute(0, 2, 1), aw.reshape(co, ci, 27).permute(0, 2, 1), 0.0)
     torch.testing.assert_close(b.grad.cpu().double(), gy.double().cpu().sum(dim=(0, 1, 2, 3)), rtol=1e-5, atol=1e-3)
+
+
+@pytest.fixture
+def no_tf32():
+    prev = torch.backends.cudnn.allow_tf32
+    torch.backends.cudnn.allow_tf32 = False
+    yield
+    torch.backends.cudnn.allow_tf32 = prev
+
+
+def test_unet_layer_shapes_at_full_size_match_torch_fp32(no_tf32):
+    """The U-Net's layer shapes at the 128^3 training size (and one 8 x 64 x 128 case), against
+    torch's FP32 convolution of the same bf16 operands on the GPU (the oracle is too slow at
+    this size). Forward and input gradient differ by the bf16 rounding of their outputs
+    (about 2^-9 relative per element, 1.7e-3 in L2); the FP32 weight gradient agrees to 1e-5."""
+    import torch.nn.functional as F
+
+    def rel(a, b):
+        return float((a.double() - b.double()).norm() / b.double().norm())
+
+    g = torch.Generator(device="cuda").manual_seed(0)
+    for (d, h, w), ci, co in [((128, 128, 128), 16, 16), ((128, 128, 128), 32, 16), ((64, 64, 64), 16, 32),
+                              ((16, 16, 16), 128, 128), ((8, 64, 128), 16, 16)]:
+        x = torch.randn((1, d, h, w, ci), device="cuda", generator=g).to(torch.bfloat16)
+        wt = (0.1 * torch.randn((co, 27, ci), device="cuda", generator=g)).to(torch.bfloat16)
+        gy = (1e-9 * torch.randn((1, d, h, w, co), device="cuda", generator=g)).to(torch.bfloat16)
+        conv.err_word("cuda").zero_()
+        y = conv.conv3d_fwd(x, wt)
+        gx = conv.conv3d_dgrad(gy, wt)
+        gw = conv.conv3d_wgrad(x, gy)
+        torch.cuda.synchronize()
+        assert int(conv.err_word("cuda").item()) == 0
+        xc, gyc, wc = to_cf(x.float()), to_cf(gy.float()), w_cf(wt.float())
+        ry = to_cf_inv(F.conv3d(xc, wc, padding=1))
+        rgx = to_cf_inv(torch.nn.grad.conv3d_input(xc.shape, wc, gyc, padding=1))
+        rgw = torch.nn.grad.conv3d_weight(xc, (co, ci, 3, 3, 3), gyc, padding=1).reshape(co, ci, 27).permute(0, 2, 1)
+        case = ((d, h, w), ci, co)
+        assert rel(y, ry) < 3e-3, case
+        assert rel(gx, rgx) < 3e-3, case
+        assert rel(gw, rgw) < 1e-4, case
