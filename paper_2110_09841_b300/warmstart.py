@@ -74,17 +74,31 @@ def generate(prob: Problem, seeds, target="phantom", tol=1e-3, max_iter=300):
     return xs, ts
 
 
-def train(model, xs, ts, epochs: int, lr: float = 1e-3, seed: int = 0, log=None):
-    """Adam on the mean squared error, one volume per step, learning rate decaying along a
-    cosine from lr to lr / 20; the network's internal scale is set to 1 / mean |target|."""
+def lr_factor(k: int, steps: int, warmup: int = 0) -> float:
+    """Learning-rate factor of step k: a linear ramp over the first `warmup` steps, then a
+    cosine from 1 down to 1/20 at step `steps` (held there afterwards)."""
+    if k < warmup:
+        return (k + 1) / warmup
+    span = max(1, steps - warmup)
+    k = min(k - warmup, span)
+    return 0.05 + 0.95 * 0.5 * (1.0 + math.cos(math.pi * k / span))
+
+
+def train(model, xs, ts, epochs: int, lr: float = 1e-3, seed: int = 0, log=None, warmup: int = 0,
+          clip: float = 0.0, log_every: int = 0):
+    """Adam on the mean squared error, one volume per step, with the learning rate of
+    lr_factor (optional linear warm-up, then a cosine from lr to lr / 20) and, if clip > 0,
+    the gradient norm clipped to clip; the network's internal scale is set to
+    1 / mean |target|. Returns the mean loss of each epoch."""
     with torch.no_grad():
         model.scale.fill_(1.0 / float(ts.abs().mean().clamp(min=1e-12)))
-    opt = torch.optim.Adam(model.parameters(), lr=lr)
+    params = [p for p in model.parameters() if p.requires_grad]
+    opt = torch.optim.Adam(params, lr=lr)
     steps = max(1, epochs * xs.shape[0])
-    sched = torch.optim.lr_scheduler.LambdaLR(
-        opt, lambda k: 0.05 + 0.95 * 0.5 * (1.0 + math.cos(math.pi * min(k, steps) / steps)))
+    sched = torch.optim.lr_scheduler.LambdaLR(opt, lambda k: lr_factor(k, steps, warmup))
     gen = torch.Generator().manual_seed(seed)
     hist = []
+    run, nrun, k = 0.0, 0, 0
     for ep in range(epochs):
         order = torch.randperm(xs.shape[0], generator=gen)
         tot = 0.0
@@ -93,9 +107,18 @@ def train(model, xs, ts, epochs: int, lr: float = 1e-3, seed: int = 0, log=None)
             out = model(xs[i:i + 1])
             loss = torch.mean((out - ts[i:i + 1]) ** 2)
             loss.backward()
+            if clip > 0.0:
+                torch.nn.utils.clip_grad_norm_(params, clip)
             opt.step()
             sched.step()
-            tot += float(loss.detach())
+            value = float(loss.detach())
+            tot += value
+            run += value
+            nrun += 1
+            k += 1
+            if log and log_every and k % log_every == 0:
+                log(f"step {k}: mean loss of the last {nrun} steps {run / nrun:.3e}")
+                run, nrun = 0.0, 0
         hist.append(tot / xs.shape[0])
         if log:
             log(f"epoch {ep}: mean loss {hist[-1]:.3e}")
@@ -149,6 +172,9 @@ def main():
     ap.add_argument("--epochs", type=int, default=3)
     ap.add_argument("--eval", type=int, default=100)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--warmup", type=int, default=0, help="steps of linear learning-rate warm-up")
+    ap.add_argument("--clip", type=float, default=0.0, help="gradient-norm clipping (0: off)")
+    ap.add_argument("--log-every", type=int, default=0, help="log the running loss every N steps")
     ap.add_argument("--variant", default="relaxed", choices=["exact", "relaxed"])
     ap.add_argument("--target", default="phantom", choices=["phantom", "cgls"])
     ap.add_argument("--out", default=None)
@@ -163,13 +189,14 @@ def main():
     t_data = time.perf_counter() - t0
     model = UNet3D().cuda()
     t0 = time.perf_counter()
-    hist = train(model, xs, ts, args.epochs, args.lr, log=print)
+    hist = train(model, xs, ts, args.epochs, args.lr, log=print, warmup=args.warmup, clip=args.clip,
+                 log_every=args.log_every)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     del xs, ts
     rows = evaluate(model, prob, range(EVAL_SEED0, EVAL_SEED0 + args.eval))
     out = {"workload": "cgls128", "variant": args.variant, "target": args.target, "train_samples": args.train,
-           "epochs": args.epochs, "lr": args.lr,
+           "epochs": args.epochs, "lr": args.lr, "warmup": args.warmup, "clip": args.clip,
            "data_s": t_data, "train_s": t_train, "loss": hist, "summary": summarise(rows), "per_seed": rows}
     print(json.dumps(out["summary"]))
     if args.out:
