@@ -84,12 +84,27 @@ def lr_factor(k: int, steps: int, warmup: int = 0) -> float:
     return 0.05 + 0.95 * 0.5 * (1.0 + math.cos(math.pi * k / span))
 
 
+def loss_value(out, target, edge_weight: float = 0.0):
+    """Mean squared error of out [n, d, h, w], plus edge_weight times the mean squared error
+    of its finite differences along each of the three axes. CGLS removes smooth errors of a
+    start in few steps but sharp ones (a blurred edge) only slowly, so weighting the
+    differences makes the start sharper where CGLS is slow."""
+    e = out - target
+    loss = torch.mean(e * e)
+    if edge_weight > 0.0:
+        for dim in (1, 2, 3):
+            d = torch.diff(e, dim=dim)
+            loss = loss + edge_weight * torch.mean(d * d)
+    return loss
+
+
 def train(model, xs, ts, epochs: int, lr: float = 1e-3, seed: int = 0, log=None, warmup: int = 0,
-          clip: float = 0.0, log_every: int = 0):
-    """Adam on the mean squared error, one volume per step, with the learning rate of
-    lr_factor (optional linear warm-up, then a cosine from lr to lr / 20) and, if clip > 0,
-    the gradient norm clipped to clip; the network's internal scale is set to
-    1 / mean |target|. Returns the mean loss of each epoch."""
+          clip: float = 0.0, log_every: int = 0, edge_weight: float = 0.0):
+    """Adam on loss_value (the mean squared error, plus edge_weight times that of the finite
+    differences), one volume per step, with the learning rate of lr_factor (optional linear
+    warm-up, then a cosine from lr to lr / 20) and, if clip > 0, the gradient norm clipped to
+    clip; the network's internal scale is set to 1 / mean |target|. Returns the mean loss of
+    each epoch."""
     with torch.no_grad():
         model.scale.fill_(1.0 / float(ts.abs().mean().clamp(min=1e-12)))
     params = [p for p in model.parameters() if p.requires_grad]
@@ -105,7 +120,7 @@ def train(model, xs, ts, epochs: int, lr: float = 1e-3, seed: int = 0, log=None,
         for i in order.tolist():
             opt.zero_grad(set_to_none=True)
             out = model(xs[i:i + 1])
-            loss = torch.mean((out - ts[i:i + 1]) ** 2)
+            loss = loss_value(out, ts[i:i + 1], edge_weight)
             loss.backward()
             if clip > 0.0:
                 torch.nn.utils.clip_grad_norm_(params, clip)
@@ -175,6 +190,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=0, help="steps of linear learning-rate warm-up")
     ap.add_argument("--clip", type=float, default=0.0, help="gradient-norm clipping (0: off)")
     ap.add_argument("--log-every", type=int, default=0, help="log the running loss every N steps")
+    ap.add_argument("--edge-weight", type=float, default=0.0,
+                    help="weight of the finite-difference term of the loss (0: plain mean squared error)")
     ap.add_argument("--variant", default="relaxed", choices=["exact", "relaxed"])
     ap.add_argument("--target", default="phantom", choices=["phantom", "cgls"])
     ap.add_argument("--out", default=None)
@@ -190,13 +207,14 @@ def main():
     model = UNet3D().cuda()
     t0 = time.perf_counter()
     hist = train(model, xs, ts, args.epochs, args.lr, log=print, warmup=args.warmup, clip=args.clip,
-                 log_every=args.log_every)
+                 log_every=args.log_every, edge_weight=args.edge_weight)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     del xs, ts
     rows = evaluate(model, prob, range(EVAL_SEED0, EVAL_SEED0 + args.eval))
     out = {"workload": "cgls128", "variant": args.variant, "target": args.target, "train_samples": args.train,
            "epochs": args.epochs, "lr": args.lr, "warmup": args.warmup, "clip": args.clip,
+           "edge_weight": args.edge_weight,
            "data_s": t_data, "train_s": t_train, "loss": hist, "summary": summarise(rows), "per_seed": rows}
     print(json.dumps(out["summary"]))
     if args.out:

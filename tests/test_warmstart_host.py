@@ -56,3 +56,27 @@ def test_summarise_counts_and_means():
     s = warmstart.summarise(rows)
     assert s["iters_zero"] == 20.5 and s["iters_warm"] == 10 and s["seeds"] == 2
     assert s["warm_faster"] == 1 and s["all_converged"] is True
+
+
+def test_loss_value_closed_form():
+    t = torch.zeros((1, 3, 4, 5))
+    ramp = 0.5 * torch.arange(5.0)                        # error grows by 0.5 per step along x
+    out = t + ramp
+    mse = float((ramp ** 2).mean())
+    assert float(warmstart.loss_value(out, t)) == pytest.approx(mse)
+    # differences: 0.5 along x, 0 along y and z
+    assert float(warmstart.loss_value(out, t, edge_weight=2.0)) == pytest.approx(mse + 2.0 * 0.25)
+    # a constant error has no differences
+    assert float(warmstart.loss_value(t + 1.0, t, edge_weight=3.0)) == pytest.approx(1.0)
+    # a checkerboard error along z: differences of 2 everywhere along z
+    chk = (-1.0) ** torch.arange(3.0)
+    assert float(warmstart.loss_value(t + chk[None, :, None, None], t, edge_weight=1.0)) == pytest.approx(1.0 + 4.0)
+
+
+def test_train_with_edge_term_fits():
+    g = torch.Generator().manual_seed(1)
+    xs = 0.01 * torch.rand((8, 4, 4, 4), generator=g)
+    ts = 3.0 * xs + 0.002
+    model = _Scale()
+    hist = warmstart.train(model, xs, ts, epochs=40, lr=5e-2, edge_weight=1.0)
+    assert hist[-1] < 1e-3 * hist[0]
