@@ -181,6 +181,18 @@ def summarise(rows):
         "warm_faster": sum(r["time_warm_s"] < r["time_zero_s"] for r in rows)}
 
 
+def save_model(model, path: str):
+    """Store the network's parameters and its input scale (FP32 master weights)."""
+    torch.save({k: v.detach().cpu() for k, v in model.state_dict().items()}, path)
+
+
+def load_model(model, path: str):
+    """Load parameters and scale written by save_model into model (on the model's device)."""
+    state = torch.load(path, map_location="cpu", weights_only=True)
+    model.load_state_dict(state)
+    return model
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=2000)
@@ -195,24 +207,34 @@ def main():
     ap.add_argument("--variant", default="relaxed", choices=["exact", "relaxed"])
     ap.add_argument("--target", default="phantom", choices=["phantom", "cgls"])
     ap.add_argument("--out", default=None)
+    ap.add_argument("--save", default=None, help="write the trained network's state to this file")
+    ap.add_argument("--load", default=None, help="evaluate the network stored in this file instead of training")
     args = ap.parse_args()
     from . import build
 
     build.build()
     g = inputs.workload_geometry("cgls128")
     prob = Problem(g, args.variant)
-    t0 = time.perf_counter()
-    xs, ts = generate(prob, range(TRAIN_SEED0, TRAIN_SEED0 + args.train), args.target)
-    t_data = time.perf_counter() - t0
     model = UNet3D().cuda()
-    t0 = time.perf_counter()
-    hist = train(model, xs, ts, args.epochs, args.lr, log=print, warmup=args.warmup, clip=args.clip,
-                 log_every=args.log_every, edge_weight=args.edge_weight)
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
-    del xs, ts
+    t_data = t_train = 0.0
+    hist = []
+    if args.load:
+        load_model(model, args.load)
+    else:
+        t0 = time.perf_counter()
+        xs, ts = generate(prob, range(TRAIN_SEED0, TRAIN_SEED0 + args.train), args.target)
+        t_data = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        hist = train(model, xs, ts, args.epochs, args.lr, log=print, warmup=args.warmup, clip=args.clip,
+                     log_every=args.log_every, edge_weight=args.edge_weight)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        del xs, ts
+    if args.save:
+        save_model(model, args.save)
     rows = evaluate(model, prob, range(EVAL_SEED0, EVAL_SEED0 + args.eval))
-    out = {"workload": "cgls128", "variant": args.variant, "target": args.target, "train_samples": args.train,
+    out = {"workload": "cgls128", "variant": args.variant, "target": args.target, "loaded": args.load,
+           "train_samples": args.train,
            "epochs": args.epochs, "lr": args.lr, "warmup": args.warmup, "clip": args.clip,
            "edge_weight": args.edge_weight,
            "data_s": t_data, "train_s": t_train, "loss": hist, "summary": summarise(rows), "per_seed": rows}

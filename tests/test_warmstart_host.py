@@ -80,3 +80,18 @@ def test_train_with_edge_term_fits():
     model = _Scale()
     hist = warmstart.train(model, xs, ts, epochs=40, lr=5e-2, edge_weight=1.0)
     assert hist[-1] < 1e-3 * hist[0]
+
+
+def test_save_and_load_round_trip(tmp_path):
+    from paper_2110_09841_b300.unet import UNet3D
+
+    a = UNet3D(seed=1)
+    with torch.no_grad():
+        a.scale.fill_(123.0)
+        a.head_w.normal_(0.0, 0.1, generator=torch.Generator().manual_seed(2))
+    path = str(tmp_path / "unet.pt")
+    warmstart.save_model(a, path)
+    b = warmstart.load_model(UNet3D(seed=9), path)
+    assert float(b.scale) == 123.0
+    for (na, ta), (nb, tb) in zip(a.state_dict().items(), b.state_dict().items()):
+        assert na == nb and torch.equal(ta, tb), na
