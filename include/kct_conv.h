@@ -1,6 +1,6 @@
 /*
  * kct_conv.h -- C ABI of the tensor-core 3D convolutions (sm_103a) used by the learned
- * warm start for CGLS (a 3D U-Net that maps the normalised backprojection A^T b / A^T 1 to
+ * warm start for CGLS (a 3D U-Net that maps the normalised backprojection A^T b / (A^T A 1) to
  * an initial guess). Not part of the projector: the paper has no learned component; it is
  * the reconstruction around the operator.
  *
