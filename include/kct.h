@@ -104,7 +104,8 @@ kct_status kct_plan_create(kct_plan **out, const kct_volume_desc *vol, const kct
                            kct_scaling scaling);
 
 /* Release the plan and its device memory. Waits for nothing: the caller must make sure no
- * work that uses the plan is still pending. NULL is accepted. */
+ * work that uses the plan is still pending. NULL is accepted. No counterpart in the paper
+ * (resource management of this library). */
 kct_status kct_plan_destroy(kct_plan *plan);
 
 /*
@@ -192,8 +193,10 @@ kct_status kct_pixel_factors(const kct_plan *plan, float *d_out, void *stream);
  */
 kct_status kct_count_pairs(const kct_plan *plan, uint64_t *count, void *stream);
 
-/* Read and clear the plan's device error word (0 = no error). Synchronises `stream`.
- * Nonzero codes: 1 = a voxel footprint larger than the kernel's bound was skipped. */
+/* Read and clear the plan's device error word (0 = no error). Synchronises `stream` (an
+ * argument beyond the minimal boundary: the word is read on the caller's stream, after the
+ * work it checks). Nonzero codes: 1 = a voxel footprint larger than the kernel's bound was
+ * skipped. No counterpart in the paper (its kernels have no error reporting). */
 kct_status kct_last_device_error(const kct_plan *plan, int32_t *code, void *stream);
 
 /*
@@ -212,11 +215,25 @@ kct_status kct_last_device_error(const kct_plan *plan, int32_t *code, void *stre
  * and must therefore come before any stream capture on that device. All calls share the
  * one array and it keeps the last call's contents (cleared where needed at each call):
  * calls that overlap on the GPU, on any streams, race and give wrong results.
- * The per-view parameters are copied from a host stack buffer with cudaMemcpyAsync.
+ * Every view is validated before anything is enqueued; the per-view parameters then reach
+ * the array as the by-value arguments of small kernels, 32 views per launch, so no host
+ * buffer has to outlive the call.
+ * A voxel whose footprint is larger than the kernel's bound is skipped and recorded in the
+ * array's error word, which kct_project_static_device_error reads.
  */
 kct_status kct_project_static(const kct_volume_desc *vol, const kct_detector_desc *det, const double *pmats,
                               int32_t nviews, kct_variant variant, kct_scaling scaling, const float *d_vol,
                               float *d_proj, int32_t accumulate, void *stream);
+
+/*
+ * Read and clear the error word of the last kct_project_static call on the current device
+ * (0 = no error; 1 = a voxel footprint larger than the kernel's bound was skipped, so the
+ * projection misses that voxel). Companion of kct_project_static, which has no plan whose
+ * error word kct_last_device_error could read; like it, this call allocates nothing. It
+ * synchronises `stream`, which should be the stream of the call it checks. No counterpart
+ * in the paper.
+ */
+kct_status kct_project_static_device_error(int32_t *code, void *stream);
 
 /*
  * CGLS reconstruction with the plan's operator: conjugate gradients on the normal equations
@@ -256,13 +273,15 @@ kct_status kct_cgls(const kct_plan *plan, const float *d_b, float *d_x, int32_t 
                     double tol, void *d_work, size_t work_bytes, double *h_normal, double *h_data,
                     kct_cgls_report *report, void *stream);
 
-/* Static description of a status code. */
+/* Static description of a status code. No counterpart in the paper (error reporting of
+ * this library). */
 const char *kct_status_string(kct_status status);
 
-/* Detail of the last failure on the calling thread ("" if none). */
+/* Detail of the last failure on the calling thread ("" if none). No counterpart in the
+ * paper. */
 const char *kct_last_error_message(void);
 
-/* KCT_VERSION of the library. */
+/* KCT_VERSION of the library. No counterpart in the paper. */
 int32_t kct_version(void);
 
 #ifdef __cplusplus

@@ -731,6 +731,17 @@ cudaError_t static_scratch(void** out) {
     return cudaSuccess;
 }
 
+// Up to 32 views' parameters, passed by value as a kernel argument (3968 bytes).
+constexpr int kStaticViewBatch = 32;
+struct StaticViewBatch {
+    View v[kStaticViewBatch];
+};
+
+// Writes the views of one batch into the array; the parameters travel with the launch.
+__global__ void static_views_kernel(StaticViewBatch batch, int nb, View* __restrict__ dst) {
+    for (int q = threadIdx.x; q < nb; q += blockDim.x) dst[q] = batch.v[q];
+}
+
 }  // namespace
 
 extern "C" kct_status kct_project_static(const kct_volume_desc* vol, const kct_detector_desc* det,
@@ -765,21 +776,24 @@ extern "C" kct_status kct_project_static(const kct_volume_desc* vol, const kct_d
     float* S = (float*)((unsigned char*)base + kStaticSumOffset);
     cudaStream_t st = (cudaStream_t)stream;
 
-    // per-view parameters, converted on the host in small batches from a stack buffer
-    View batch[32];
-    for (int q0 = 0; q0 < nviews; q0 += 32) {
-        const int nb = (nviews - q0 < 32) ? nviews - q0 : 32;
-        for (int q = 0; q < nb; ++q) {
-            std::string why = setup_view(pmats + 12 * (size_t)(q0 + q), *vol, batch[q]);
-            if (!why.empty()) {
-                char buf[64];
-                std::snprintf(buf, sizeof buf, "view %d: ", q0 + q);
-                bool unsup = why.compare(0, 12, "unsupported:") == 0;
-                return fail(unsup ? KCT_ERR_UNSUPPORTED : KCT_ERR_GEOMETRY, buf + why);
-            }
+    // per-view parameters: every view is validated first, so that a rejected geometry
+    // enqueues nothing; then they go to the array in batches of 32, each batch as the
+    // by-value argument of one small kernel (no host buffer has to outlive the call)
+    StaticViewBatch batch;
+    for (int q = 0; q < nviews; ++q) {
+        std::string why = setup_view(pmats + 12 * (size_t)q, *vol, batch.v[0]);
+        if (!why.empty()) {
+            char buf[64];
+            std::snprintf(buf, sizeof buf, "view %d: ", q);
+            bool unsup = why.compare(0, 12, "unsupported:") == 0;
+            return fail(unsup ? KCT_ERR_UNSUPPORTED : KCT_ERR_GEOMETRY, buf + why);
         }
-        // a pageable source is copied out before the call returns, so the batch can be reused
-        e = cudaMemcpyAsync(d_views + q0, batch, sizeof(View) * nb, cudaMemcpyHostToDevice, st);
+    }
+    for (int q0 = 0; q0 < nviews; q0 += kStaticViewBatch) {
+        const int nb = (nviews - q0 < kStaticViewBatch) ? nviews - q0 : kStaticViewBatch;
+        for (int q = 0; q < nb; ++q) setup_view(pmats + 12 * (size_t)(q0 + q), *vol, batch.v[q]);
+        static_views_kernel<<<1, 32, 0, st>>>(batch, nb, d_views + q0);
+        e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "uploading view parameters");
     }
     Grid G;
@@ -809,5 +823,22 @@ extern "C" kct_status kct_project_static(const kct_volume_desc* vol, const kct_d
         kct::scale_kernel<0><<<sgrid, 256, 0, st>>>(d_views, G, S, d_proj, accumulate ? 1 : 0);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "pixel factor launch");
+    return KCT_OK;
+}
+
+extern "C" kct_status kct_project_static_device_error(int32_t* code, void* stream) {
+    g_last_error.clear();
+    if (!code) return fail(KCT_ERR_INVALID_ARG, "null output pointer");
+    void* base = nullptr;
+    cudaError_t e = static_scratch(&base);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
+    int* d_err = (int*)((unsigned char*)base + kStaticErrOffset);
+    cudaStream_t st = (cudaStream_t)stream;
+    int h = 0;
+    e = cudaMemcpyAsync(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
+    *code = h;
     return KCT_OK;
 }

@@ -26,7 +26,8 @@ EXPORTED = ["kct_plan_create", "kct_plan_destroy", "kct_project", "kct_backproje
             "kct_pixel_factors", "kct_count_pairs", "kct_last_device_error", "kct_status_string",
             "kct_last_error_message", "kct_version", "kct_project_static", "kct_project_batch",
             "kct_backproject_batch", "kct_cgls_workspace_bytes", "kct_cgls", "kct_plan_autotune",
-            "kct_plan_set_view_chunk", "kct_plan_get_view_chunk", "kct_siddon_project"]
+            "kct_plan_set_view_chunk", "kct_plan_get_view_chunk", "kct_siddon_project",
+            "kct_project_static_device_error"]
 
 
 class KctError(RuntimeError):
@@ -91,6 +92,8 @@ def load(path: str | None = None):
         lib.kct_project_static.argtypes = [ctypes.POINTER(VolumeDesc), ctypes.POINTER(DetectorDesc), V, I32, I, I,
                                            V, V, I32, V]
         lib.kct_project_static.restype = I
+        lib.kct_project_static_device_error.argtypes = [ctypes.POINTER(I32), V]
+        lib.kct_project_static_device_error.restype = I
         lib.kct_siddon_project.argtypes = [V, V, V, I32, I32, V]
         lib.kct_siddon_project.restype = I
         lib.kct_plan_autotune.argtypes = [V, V, V, ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_float), V]

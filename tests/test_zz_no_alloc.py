@@ -30,6 +30,13 @@ def call_static(lib, g, variant, scaling, x, out, accumulate=0):
                                   ctypes.c_void_p(out.data_ptr()), accumulate, stream)
 
 
+def static_error(lib):
+    code = ctypes.c_int32(-1)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.kct_project_static_device_error(ctypes.byref(code), stream) == 0
+    return int(code.value)
+
+
 def assert_close_per_view(g, o, tol=TOL):
     g = np.asarray(g, dtype=np.float64)
     o = np.asarray(o, dtype=np.float64)
@@ -50,11 +57,13 @@ def test_static_matches_planned_projection(variant, vname):
     for _ in range(2):
         out = torch.full(g.proj_shape, 7.0, dtype=torch.float32, device="cuda")
         assert call_static(lib, g, variant, 0, x, out) == 0, lib.kct_last_error_message()
+        assert static_error(lib) == 0
         torch.cuda.synchronize()
         assert_close_per_view(out.cpu().numpy(), ref.cpu().numpy())
     # accumulate adds to the output
     out = torch.full(g.proj_shape, 0.5, dtype=torch.float32, device="cuda")
     assert call_static(lib, g, variant, 0, x, out, accumulate=1) == 0
+    assert static_error(lib) == 0
     torch.cuda.synchronize()
     assert_close_per_view(out.cpu().numpy() - 0.5, ref.cpu().numpy())
 
@@ -66,3 +75,23 @@ def test_static_rejects_requests_beyond_its_array():
     out = torch.zeros(1, dtype=torch.float32, device="cuda")
     assert call_static(lib, g, 0, 0, x, out) == 6
     assert b"8388608" in lib.kct_last_error_message()
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_static_reports_a_skipped_footprint(variant):
+    """A 1 mm voxel seen through 0.0002 mm wide pixels covers about 8000 detector columns,
+    more than the kernel's bound (4096): the voxel is skipped, the array's error word says
+    so, and the next call starts from a cleared word."""
+    lib = load()
+    P = inputs.circular_pmats(1, 400.0, 600.0, 9000, 16, 0.0002, 0.25)
+    g = inputs.Geometry(1, 1, 1, 1.0, 1.0, 1.0, 9000, 16, 0.0002, 0.25, P)
+    x = torch.ones(g.vol_shape, dtype=torch.float32, device="cuda")
+    out = torch.zeros(g.proj_shape, dtype=torch.float32, device="cuda")
+    assert call_static(lib, g, variant, 0, x, out) == 0, lib.kct_last_error_message()
+    assert static_error(lib) == 1
+    assert float(out.abs().max()) == 0.0
+    g32 = inputs.workload_geometry("cvp32")
+    x32 = inputs.workload_phantom("cvp32").cuda()
+    out32 = torch.zeros(g32.proj_shape, dtype=torch.float32, device="cuda")
+    assert call_static(lib, g32, variant, 0, x32, out32) == 0
+    assert static_error(lib) == 0
