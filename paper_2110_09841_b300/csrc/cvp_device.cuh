@@ -58,12 +58,16 @@ struct View {
     float tmin_sq, tmax_sq;      // t' range of the square
     float sq_tt, sq_tx;          // Green sums of the full square for t'^2 and t' xi'
     float sx, sy;                // source s_1, s_2 (used by the ray-driven comparator only)
+    float cv_lo, inv_agv_lo;     // low-order parts of cv and 1/|gv|
+    float sz_lo;                 // low-order part of s_3
 };
 
 struct Grid {
     int nx, ny, nz, nu, nv, nviews;
     float ax, ay, az;
     float x0, y0, z0;            // centre of voxel (0, 0, 0)
+    double axd, ayd, azd;        // the same in double precision (exact geometry of faces and columns)
+    double x0d, y0d, z0d;
 };
 
 constexpr int KCT_CB = 8;        // column boundaries handled per pass (7 columns)
@@ -205,6 +209,31 @@ KCT_HD int clip_square(const View& V, const Line& l0, const Line& l1, float* pt,
 // Column setup: the voxel column (i, j) in one view
 // ----------------------------------------------------------------------------------------
 
+// A float pair (hi, lo) holding hi + lo to about twice float precision (used where a small
+// height is the difference of two large coordinates).
+struct F2 {
+    float hi, lo;
+};
+
+KCT_HD F2 f2_of(double d) {
+    const float h = (float)d;
+    return F2{h, (float)(d - (double)h)};
+}
+
+// a + b c for an integer-valued float b: the product split exactly by an FMA, the sum by
+// Knuth's two-sum
+KCT_HD F2 f2_axpy(F2 a, float b, F2 c) {
+    const float p = b * c.hi;
+    const float pe = fmaf(b, c.hi, -p);
+    const float s = a.hi + p;
+    const float z = s - a.hi;
+    const float e = (a.hi - (s - z)) + (p - z);
+    return F2{s, a.lo + fmaf(b, c.lo, pe + e)};
+}
+
+// (a - b) rounded to float; the large parts cancel exactly when a and b are close
+KCT_HD float f2_diff(F2 a, F2 b) { return (a.hi - b.hi) + (a.lo - b.lo); }
+
 struct Column {
     float tc, xc;        // depth and lateral offset of the column centre
     float itc;           // 1 / tc
@@ -212,6 +241,7 @@ struct Column {
     float gxi;           // gu / tc
     float umin, umax;    // u range of the base square
     int n_first, n_last; // detector columns touched (clipped), n_first > n_last if none
+    F2 da;               // tc / |gv|: height per detector row at the column centre depth (two floats)
 };
 
 KCT_HD bool column_setup(const View& V, const Grid& G, int i, int j, Column& C) {
@@ -239,6 +269,10 @@ KCT_HD bool column_setup(const View& V, const Grid& G, int i, int j, Column& C) 
     int n0 = (int)floorf(umin + 0.5f), n1 = (int)floorf(umax + 0.5f);
     C.n_first = max(n0, 0);
     C.n_last = min(n1, G.nu - 1);
+    const double tcd = fma((double)V.wx + (double)V.wx_lo, fma((double)i, G.axd, G.x0d),
+                           fma((double)V.wy + (double)V.wy_lo, fma((double)j, G.ayd, G.y0d),
+                               (double)V.aw + (double)V.aw_lo));
+    C.da = f2_of(tcd * ((double)V.inv_agv + (double)V.inv_agv_lo));
     return C.n_first <= C.n_last;
 }
 

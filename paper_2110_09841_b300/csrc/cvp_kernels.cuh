@@ -73,7 +73,7 @@ struct WarpSmem {
 // blocks stay small.
 struct WarpSmemRelaxed {
     Column C;
-    float4 fa[KCT_CB];             // A_n, t_n, 1/t_n, half the voxel's projected row extent
+    float4 fa[KCT_CB];             // A_n, t' of its centre of mass, 1/t_n, half the voxel's projected row extent
 };
 
 struct Tile {                      // detector window covered by a brick in one view
@@ -168,6 +168,21 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
     const float az = G.az;
     const float dp0 = C.tc * V.inv_agv, dp1 = V.inv_agv;   // change of p0, p1 from one row boundary to the next
     const float vtiny = 1e-9f * G.ax * G.ay * az;
+    // Height offset of row boundary m - 1/2 over the centre of voxel k at the column centre depth,
+    // tc (m - 1/2 - cv) / |gv| - sign(gv) zeta_k, in two-float arithmetic: its two terms are large
+    // and nearly cancel, and thin slivers (a plane close to a face) need the difference to float
+    // precision. A plane b rows higher is then az/2 + b dp0 + offset (small terms, plain float).
+    const F2 z0s = f2_of(G.z0d - ((double)V.sz + (double)V.sz_lo)), azF = f2_of(G.azd);
+    auto row_offset = [&](int k, int m) -> float {
+        const F2 zc = f2_axpy(z0s, (float)k, azF);
+        const F2 sg = V.sgv > 0.f ? zc : F2{-zc.hi, -zc.lo};
+        // (m - 1/2 - cv) da: m - 1/2 is exact, cv and da carry low-order parts (two-sum, two-product)
+        const float a = (float)m - 0.5f, s = a - V.cv, bb = s - a;
+        const float dvl = ((a - (s - bb)) + (-V.cv - bb)) - V.cv_lo;
+        const float ph = s * C.da.hi;
+        const F2 a0 = F2{ph, fmaf(s, C.da.hi, -ph) + fmaf(s, C.da.lo, dvl * C.da.hi)};
+        return f2_diff(a0, sg);
+    };
     // the lane's voxels kbase + lane + 32 p; their crossing planes share one queue round
 #pragma unroll
     for (int p = 0; p < KPL; ++p) {
@@ -180,6 +195,7 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
         const float tlo = fb.y, thi = fb.z;
         const float2 fr = ws->fr[c];
         int m_first[KPL], R[KPL];
+        float off0p[KPL];
         unsigned cross[KPL], zero[KPL], full[KPL];
         int nev[KPL];
 #pragma unroll
@@ -201,7 +217,8 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
                 if (R[p] < 0) R[p] = 0;
             }
             // height of {v < V_b} over t' is p0 + p1 t', p0 = az/2 + tc (V_b - v_c)/|gv|, p1 = (V_b - cv)/|gv|
-            const float off0 = C.tc * (-fmaf(V.gv, zc * C.itc, V.cv - ((float)m_first[p] - 0.5f))) * V.inv_agv;
+            const float off0 = row_offset(k, m_first[p]);
+            off0p[p] = off0;
             const float p1_0 = ((float)m_first[p] - 0.5f - V.cv) * V.inv_agv;
             // classes of the boundaries: 0 / az for planes outside the voxel, crossing mask
             unsigned cr = 0u, ze = 0u, fu = 0u;
@@ -254,14 +271,13 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
                         const int k = kbase + p * 32 + lane;
                         const float zc = fmaf((float)k, az, G.z0) - V.sz;
                         const float zs = zc * V.sgv;
-                        const float off0 = C.tc * (-fmaf(V.gv, zc * C.itc, V.cv - ((float)m_first[p] - 0.5f))) * V.inv_agv;
                         const float p1_0 = ((float)m_first[p] - 0.5f - V.cv) * V.inv_agv;
                         const int rb = (R[p] + 1) >> 1;
                         const unsigned mbot = cross[p] & ((2u << rb) - 1u), mtop = cross[p] & ~((1u << rb) - 1u);
                         const int nbot = __popc(mbot);
                         for (unsigned m = cross[p]; m; m &= m - 1u) {
                             const int b = __ffs(m) - 1;
-                            const float p0 = fmaf(0.5f, az, fmaf((float)b, dp0, off0)), p1 = fmaf((float)b, dp1, p1_0);
+                            const float p0 = fmaf(0.5f, az, fmaf((float)b, dp0, off0p[p])), p1 = fmaf((float)b, dp1, p1_0);
                             if (b <= rb) {
                                 const int q = ep + __popc(mbot & ((1u << b) - 1u));
                                 ws->ev_p0[q] = p0;
@@ -313,7 +329,6 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
                     const float bc = zc * C.itc;
                     const float zs = zc * V.sgv;
                     const float D2 = fmaf(C.tc, C.tc, fmaf(C.xc, C.xc, zc * zc));
-                    const float off0 = C.tc * (-fmaf(V.gv, bc, V.cv - ((float)m_first[p] - 0.5f))) * V.inv_agv;
                     const float p1_0 = ((float)m_first[p] - 0.5f - V.cv) * V.inv_agv;
                     const int rb = (R[p] + 1) >> 1;
                     const unsigned mbot = cross[p] & ((2u << rb) - 1u), mtop = cross[p] & ~((1u << rb) - 1u);
@@ -346,7 +361,7 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
                                 if (h == 0 && reuse) continue;
                                 const int b = r + h;
                                 const unsigned bit = 1u << b;
-                                float p0 = fmaf(0.5f, az, fmaf((float)b, dp0, off0)), p1 = fmaf((float)b, dp1, p1_0);
+                                float p0 = fmaf(0.5f, az, fmaf((float)b, dp0, off0p[p])), p1 = fmaf((float)b, dp1, p1_0);
                                 if (zero[p] & bit) { p0 = 0.f; p1 = 0.f; }
                                 if (full[p] & bit) { p0 = az; p1 = 0.f; }
                                 // the linear form in the row's frame is evaluated by every lane (no
@@ -391,6 +406,8 @@ __device__ __forceinline__ void relaxed_voxels(const View& V, const Grid& G, con
                                                int kbase, int lane, const WarpSmemRelaxed* ws, Sink& sink,
                                                int* err) {
     const float az = G.az;
+    const F2 z0s = f2_of(G.z0d - ((double)V.sz + (double)V.sz_lo)), azF = f2_of(G.azd);
+    const float ida = __frcp_rn(C.da.hi);
     for (int pass = 0; pass < KPL; ++pass) {
         const int k = kbase + pass * 32 + lane;
         if (k >= G.nz) continue;
@@ -398,16 +415,26 @@ __device__ __forceinline__ void relaxed_voxels(const View& V, const Grid& G, con
         const float zc = fmaf((float)k, az, G.z0) - V.sz;
         const float iD2 = 1.0f / fmaf(C.tc, C.tc, fmaf(C.xc, C.xc, zc * zc));
         const float gz = V.gv * zc;
+        // Row offset of the voxel centre at the column centre depth, vc = gv zeta / tc =
+        // sign(gv) zeta / da, and B = -cv - vc in two floats: the distance of row boundary m from
+        // the voxel centre's projection, m + B + vc delta (delta = t'_CM / t_n), is a small
+        // difference of large row coordinates, and thin slivers need it to float precision.
+        const F2 zf = f2_axpy(z0s, (float)k, azF);
+        const float q0 = zf.hi * ida;                                       // zeta / da, then its residual
+        const float q1 = (fmaf(-q0, C.da.hi, zf.hi) + fmaf(-q0, C.da.lo, zf.lo)) * ida;
+        const float vch = V.sgv * q0, vcl = V.sgv * q1;
+        const float bs = -V.cv - vch, bz = bs + V.cv;
+        const float bl = ((-V.cv - (bs - bz)) + (-vch - bz)) - V.cv_lo - vcl;
         for (int c = 0; c < ncol; ++c) {
-            const float4 fa = ws->fa[c];           // A_n, t_n, 1/t_n, hv
+            const float4 fa = ws->fa[c];           // A_n, t'_CM, 1/t_n, hv
             if (!(fa.x > 0.f)) continue;
             const float hv = fa.w;
             const float vn = fmaf(gz, fa.z, V.cv);
             const int m_first = max((int)floorf(vn - hv + 0.5f), 0);
             const int m_last = min((int)floorf(vn + hv + 0.5f), G.nv - 1);
             if (m_last - m_first + 2 > KCT_ROWS) { atomicOr(err, 1); continue; }
-            const float w = fa.x * fa.y * V.inv_agv * iD2;
-            float e = -fmaf(gz, fa.z, V.cv - (float)m_first);   // m_first - v_n
+            const float w = fa.x * (C.tc + fa.y) * V.inv_agv * iD2;
+            float e = ((float)m_first + bs) + fmaf(vch, fa.y * fa.z, bl);   // m_first - v_n
             const int n = cstart + c;
             for (int m = m_first; m <= m_last; ++m, e += 1.0f) {
                 const float d = fminf(hv, e + 0.5f) - fmaxf(-hv, e - 0.5f);
@@ -434,9 +461,9 @@ __device__ __noinline__ void build_column_cut(const View* Vp, const Column* Cp, 
         seg_acc<false>(g, pt[e], px[e], pt[f], px[f]);
     }
     const float m1 = 0.5f * g.a, mt = g.t * (1.f / 6.f);
-    const float tn = C.tc + (m1 > 0.f ? mt / m1 : 0.f);
-    const float itn = 1.0f / tn;
-    ws->fa[c] = make_float4(m1, tn, itn, 0.5f * az * fabsf(V.gv) * itn);
+    const float tcm = m1 > 0.f ? mt / m1 : 0.f;            // t' of the centre of mass of H_n
+    const float itn = 1.0f / (C.tc + tcm);
+    ws->fa[c] = make_float4(m1, tcm, itn, 0.5f * az * fabsf(V.gv) * itn);
 }
 
 // H_n for detector column n, near-exact variant: its vertices, the Green terms of its edges,

@@ -163,7 +163,19 @@ std::string setup_view(const double* P, const kct_volume_desc& vol, View& V) {
     V.sq_tx = (float)stx;
     V.sx = (float)s[0];
     V.sy = (float)s[1];
+    V.cv_lo = (float)(cv - (double)V.cv);
+    V.inv_agv_lo = (float)(1.0 / std::fabs(gv) - (double)V.inv_agv);
+    V.sz_lo = (float)(s[2] - (double)V.sz);
     return std::string();
+}
+
+void set_grid_doubles(Grid& G, const kct_volume_desc& vol) {
+    G.axd = vol.ax;
+    G.ayd = vol.ay;
+    G.azd = vol.az;
+    G.x0d = 0.5 * (1 - vol.nx) * vol.ax;
+    G.y0d = 0.5 * (1 - vol.ny) * vol.ay;
+    G.z0d = 0.5 * (1 - vol.nz) * vol.az;
 }
 
 unsigned bricks(const Grid& G) {
@@ -332,6 +344,7 @@ kct_status kct_plan_create(kct_plan** out, const kct_volume_desc* vol, const kct
     G.x0 = (float)(0.5 * (1 - vol->nx) * vol->ax);
     G.y0 = (float)(0.5 * (1 - vol->ny) * vol->ay);
     G.z0 = (float)(0.5 * (1 - vol->nz) * vol->az);
+    set_grid_doubles(G, *vol);
 
     cudaError_t e = cudaGetDevice(&p->device);
     if (e != cudaSuccess) { delete p; return cuda_fail(e, "cudaGetDevice"); }
@@ -731,7 +744,7 @@ cudaError_t static_scratch(void** out) {
     return cudaSuccess;
 }
 
-// Up to 32 views' parameters, passed by value as a kernel argument (3968 bytes).
+// Up to 32 views' parameters, passed by value as a kernel argument (about 4.4 KB).
 constexpr int kStaticViewBatch = 32;
 struct StaticViewBatch {
     View v[kStaticViewBatch];
@@ -803,6 +816,7 @@ extern "C" kct_status kct_project_static(const kct_volume_desc* vol, const kct_d
     G.x0 = (float)(0.5 * (1 - vol->nx) * vol->ax);
     G.y0 = (float)(0.5 * (1 - vol->ny) * vol->ay);
     G.z0 = (float)(0.5 * (1 - vol->nz) * vol->az);
+    set_grid_doubles(G, *vol);
     // the array keeps the previous call's contents: clear the sums and the error word
     e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(S, 0, sizeof(float) * (size_t)npix, st);

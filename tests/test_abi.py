@@ -118,3 +118,4 @@ def test_rejects_geometry_outside_the_arrangement(lib):
     assert st in (0, 3)      # 3 only where no GPU is present
     if st == 0:
         lib.kct_plan_destroy(h)
+

@@ -131,6 +131,46 @@ def test_single_voxel_and_accumulate(vname, variant):
     assert abs(float(xb.cpu()[0, 0, 0]) - refx[0, 0, 0]) <= 1e-5 * refx[0, 0, 0]
 
 
+@pytest.mark.parametrize("vname,variant", VARIANTS)
+def test_rows_along_plus_x3(vname, variant):
+    """Detector row index growing with x_3 (the v axis flipped: v' = nv - 1 - v), the other
+    orientation of the paper's arrangement; forward and adjoint against the oracle."""
+    g = inputs.make_geometry((13, 7, 11), (0.9, 1.3, 0.7), (17, 15), (0.7, 0.9), 4, 300.0, 500.0, 360.0)
+    P = g.pmats.copy()
+    P[:, 1, :] = (g.nv - 1) * P[:, 2, :] - P[:, 1, :]
+    g = inputs.Geometry(**{**g.__dict__, "pmats": P})
+    x = np.random.default_rng(13).random(g.vol_shape)
+    y = np.random.default_rng(14).random(g.proj_shape)
+    for sname, scaling in SCALINGS:
+        A = Projector(g, vname, sname)
+        b = A.project(dev(x)).cpu().numpy()
+        assert_close_per_view(b, oracle.project(g, x, variant, scaling))
+        xb = A.backproject(dev(y)).cpu().numpy()
+        assert_close_volume(xb, oracle.backproject(g, y, variant, scaling))
+        assert A.device_error() == 0
+
+
+@pytest.mark.parametrize("vname,variant", VARIANTS)
+def test_elevated_source_thin_slivers(vname, variant):
+    """Source 100 mm below the volume centre, so that row boundaries meet the voxels about
+    100 mm above the source plane: a boundary's height over a voxel face is then the small
+    difference of two ~100 mm coordinates. The detector cuts the footprints into thin slivers
+    at its edge rows; forward and adjoint against the oracle element by element."""
+    P = inputs.circular_pmats(4, 300.0, 500.0, 17, 16, 0.7, 0.9, 360.0, 10.0, cv=197.0)
+    P[:, :, 3] -= P[:, :, :3] @ np.array([0.0, 0.0, -100.0])
+    g = inputs.Geometry(13, 7, 11, 0.9, 1.3, 0.7, 17, 16, 0.7, 0.9, P)
+    x = np.random.default_rng(21).random(g.vol_shape)
+    y = np.random.default_rng(22).random(g.proj_shape)
+    A = Projector(g, vname, "cos")
+    b = A.project(dev(x)).cpu().numpy()
+    ref = oracle.project(g, x, variant, 0)
+    assert all(np.abs(ref[v]).max() > 0 for v in range(g.nviews))
+    assert_close_per_view(b, ref)
+    xb = A.backproject(dev(y)).cpu().numpy()
+    assert_close_volume(xb, oracle.backproject(g, y, variant, 0))
+    assert A.device_error() == 0
+
+
 def test_volume_off_detector_gives_zeros():
     # a detector far off to the side: no voxel projects onto it
     P = inputs.circular_pmats(2, 300.0, 500.0, 16, 16, 0.5, 0.5, cu=-400.0)
