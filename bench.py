@@ -31,8 +31,7 @@ METRIC = "CVP project+backproject Gvoxel·views/s at 512³×496 views; CGLS time
 UNIT = "Gvoxel·views/s"
 
 # Per-kernel counts from one ncu capture of each projector kernel on the benchmark geometry
-# restricted to 8 of its views (python bench.py --profile-case cvp512 --views 8 ...; see
-# profiles/projector_kernels_cvp512_8views.md):
+# restricted to 8 of its views (python bench.py --profile-case cvp512 --views 8 ...):
 #   flop_per_vv  FP32 operations (thread-level FADD + FMUL + 2 FFMA) per voxel-view,
 #   warp_per_vv  warp instructions issued per voxel-view, simt: active lanes per instruction / 32,
 #   dram_8       DRAM bytes read + written by that 8-view launch.
@@ -75,11 +74,16 @@ def parse(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cgls", action="store_true")
     ap.add_argument("--accuracy", action="store_true",
-                    help="compare both variants and scalings with 64-ray supersampled ray integration and exit")
+                    help="compare both variants and scalings with supersampled ray integration (K = 32, 64) and exit")
     ap.add_argument("--convs", action="store_true",
                     help="time the warm-start U-Net's tensor-core convolutions at 128^3 and exit")
     ap.add_argument("--paper-geometries", action="store_true",
                     help="time P and BP at the geometries of the paper's Tables I and II and exit")
+    ap.add_argument("--throughput", default=None, metavar="WORKLOAD",
+                    help="time P and BP of both variants at one workload (with nonzero pairs per second) and exit")
+    ap.add_argument("--batch", action="store_true",
+                    help="batched operator: 8 perfusion frames of 256^3 through 248 views, P + BP captured in a "
+                         "CUDA graph and replayed, and exit")
     ap.add_argument("--cgls-max-iter", type=int, default=200)
     ap.add_argument("--profile-case", default=None, metavar="WORKLOAD",
                     help="run one projector call on a sub-sampled workload (for ncu captures) and exit")
@@ -450,12 +454,16 @@ def run_kct(args):
               "peak_per_s": sms * 4 * clk, "frac": wpv * geom.voxel_views / (dom_ms / 1e3) / (sms * 4 * clk),
               "simt_efficiency": NCU[name]["simt"], "basis": "ncu warp instruction count x event-timed launch"}
              if wpv else None)
-    roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "measured_fp32_fma_tflops": fp32_probe, "issue": issue,
-                "frac": (achieved / peak_tflops) if achieved else None, "traffic": traffic,
+    # the peak is the FP32 FMA rate measured on this GPU by the probe kernel (at the running clock);
+    # the derived SMs x 128 lanes x 2 FLOP x max clock figure is kept beside it
+    peak = fp32_probe if fp32_probe else peak_tflops
+    roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "peak_derived_tflops": peak_tflops, "issue": issue,
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "traffic_unit": "bytes per launch (ncu, 8-view capture scaled to the full launch)",
                 "launch_ms": dom_ms, "flop_per_voxel_view": flop_vv,
-                "peak_basis": f"FP32 FMA: {sms} SMs x 128 lanes x 2 FLOP x {max_mhz:.0f} MHz (derived; measured_fp32_fma_tflops is the probe kernel at the running clock)"}
+                "peak_basis": ("measured: FP32 FMA probe kernel on this GPU" if fp32_probe else
+                               f"derived (probe unavailable): {sms} SMs x 128 lanes x 2 FLOP x {max_mhz:.0f} MHz")}
 
     cb_val, cb_desc, cb_threads = cpu_baseline(geom, 10.0)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -483,6 +491,101 @@ PAPER_GVV_S = {
                      "relaxed": {"project": 0.224, "backproject": 0.409},
                      "source": "Sec. IV-A Table II, AMD Radeon VII"},
 }
+
+
+def time_calls(call, reps: int = 3) -> float:
+    """ms per call: one warm-up call, then reps calls between CUDA events on the current stream."""
+    import torch
+
+    call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        call()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_throughput(args):
+    """P and BP of both variants at one workload (seeded phantom, U[0,1) projections; one
+    warm-up and three timed calls each, CUDA events), with the number of nonzero voxel-pixel
+    pairs counted on the device and the pairs per second it implies."""
+    import torch
+
+    from paper_2110_09841_b300 import build, inputs
+    from paper_2110_09841_b300.kct import Projector
+
+    build.build()
+    name = args.throughput
+    g = inputs.workload_geometry(name)
+    x = inputs.workload_phantom(name, device="cuda")
+    y = inputs.uniform_projections(g.proj_shape, 2024, device="cuda")
+    out = {"mode": "throughput", "workload": name, "voxel_views": g.voxel_views, "scaling": args.scaling,
+           "unit": UNIT, "results": {}}
+    for v in ("exact", "relaxed"):
+        A = Projector(g, v, args.scaling)
+        b = torch.empty(g.proj_shape, device="cuda")
+        xb = torch.empty(g.vol_shape, device="cuda")
+        nnz = A.count_pairs()
+        r = {"nnz_pairs": nnz, "pairs_per_voxel_view": nnz / g.voxel_views}
+        for d, call in (("project", lambda: A.project(x, out=b)), ("backproject", lambda: A.backproject(y, out=xb))):
+            ms = time_calls(call)
+            r[d] = {"ms": ms, "gvv_s": g.voxel_views / (ms / 1e3) / 1e9, "gpairs_s": nnz / (ms / 1e3) / 1e9}
+        assert A.device_error() == 0
+        out["results"][v] = r
+    print(json.dumps(out), flush=True)
+
+
+def run_batch(args):
+    """The batched operator: 8 perfusion-like frames of 256^3 (one seeded phantom plus five
+    vessel ellipsoids with Gaussian bolus curves) through 248 shared views over 200 deg onto a
+    616x480 detector. The forward view chunk is autotuned on one frame; then one batched
+    projection and one batched backprojection of its result (one launch each) are captured in
+    a CUDA graph, which is replayed: time per replay from CUDA events around 5 replays after a
+    warm-up replay. Throughput counts 8 frames x 256^3 voxels x 248 views per direction."""
+    import torch
+
+    from paper_2110_09841_b300 import build, inputs
+    from paper_2110_09841_b300.kct import Projector
+
+    build.build()
+    g = inputs.workload_geometry("cvp256")
+    nb = 8
+    frames = inputs.perfusion_frames(g, 4004, frames=nb, device="cuda")
+    proj = torch.empty((nb,) + g.proj_shape, device="cuda")
+    back = torch.empty((nb,) + g.vol_shape, device="cuda")
+    units = nb * g.voxel_views
+    out = {"mode": "batch", "workload": "8 perfusion frames of 256^3 @ 0.5 mm, 248 views / 200 deg, SID 750 / "
+           "SDD 1200 mm, 616x480 detector @ 0.616 mm", "scaling": args.scaling, "unit": UNIT, "results": {}}
+    for v in ("exact", "relaxed"):
+        A = Projector(g, v, args.scaling)
+        chunk, tune_ms = A.autotune(frames[0].contiguous())
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            A.project_batch(frames, out=proj)
+            A.backproject_batch(proj, out=back)
+        torch.cuda.current_stream().wait_stream(s)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            A.project_batch(frames, out=proj)
+            A.backproject_batch(proj, out=back)
+        ms = time_calls(graph.replay, reps=5)
+        # eager timing of each direction, and the replay checked against eager calls
+        ms_p = time_calls(lambda: A.project_batch(frames, out=proj))
+        ms_b = time_calls(lambda: A.backproject_batch(proj, out=back))
+        graph.replay()
+        torch.cuda.synchronize()
+        ref = A.backproject_batch(A.project_batch(frames))
+        agree = float((back - ref).abs().max() / ref.abs().max())
+        assert A.device_error() == 0
+        out["results"][v] = {"view_chunk": chunk, "graph_replay_ms": ms, "gvv_s_p_plus_bp": 2 * units / (ms / 1e3) / 1e9,
+                             "project_ms": ms_p, "project_gvv_s": units / (ms_p / 1e3) / 1e9,
+                             "backproject_ms": ms_b, "backproject_gvv_s": units / (ms_b / 1e3) / 1e9,
+                             "replay_vs_eager_max_rel": agree}
+    print(json.dumps(out), flush=True)
 
 
 def run_paper_geometries(args):
@@ -563,35 +666,39 @@ def run_convs(args):
 
 
 def run_accuracy(args):
-    """Accuracy of the CVP variants against supersampled ray integration (K x K = 64 rays per
-    pixel, exact path lengths; equal weights for the cos scaling, solid-angle weights for the
-    exact scaling), on 8 evenly spaced views of the 512^3 workloads (7 deg and 20 deg half
-    cone angle). Errors: |b - ref|_2 / |ref|_2 and max |b - ref| / max |ref| per workload."""
+    """Accuracy of the CVP variants against supersampled ray integration (K x K rays per pixel,
+    exact path lengths; equal weights for the cos scaling, solid-angle weights for the exact
+    scaling) on 8 evenly spaced views of the 512^3 workloads (7 deg and 20 deg half cone
+    angle), with references at K = 32 and K = 64: the difference between the two references
+    bounds what the comparison resolves. Errors: |b - ref|_2 / |ref|_2 and max |b - ref| /
+    max |ref| over the pixels of the 8 views."""
     import torch
 
     from paper_2110_09841_b300 import build, inputs
     from paper_2110_09841_b300.kct import Projector
 
     build.build()
-    out = {"mode": "accuracy", "reference": "K x K = 8 x 8 rays per pixel, exact path lengths", "results": {}}
+    ks = (32, 64)
+    out = {"mode": "accuracy", "reference": "K x K rays per pixel, exact path lengths, K = 32 and 64", "results": {}}
     for name in ("cvp512", "cvp512wide"):
         g = inputs.workload_geometry(name)
         g = g.subset_views(list(range(0, g.nviews, g.nviews // 8))[:8])
         x = inputs.workload_phantom(name, device="cuda")
-        ref = {False: None, True: None}
-        res = {}
-        for weighted in (False, True):
-            ref[weighted] = Projector(g, "exact", "cos").siddon(x, K=8, weighted=weighted)
-        one = Projector(g, "exact", "cos").siddon(x, K=1)
+        R = Projector(g, "exact", "cos")
+        ref = {(K, w): R.siddon(x, K=K, weighted=w) for K in ks for w in (False, True)}
+        one = R.siddon(x, K=1)
 
         def err(b, r):
             return {"rel_l2": float((b - r).norm() / r.norm()), "rel_max": float((b - r).abs().max() / r.abs().max())}
 
-        res["single_ray"] = err(one, ref[False])
+        res = {"single_ray_vs_K64": err(one, ref[(64, False)]),
+               "K32_vs_K64_equal_weights": err(ref[(32, False)], ref[(64, False)]),
+               "K32_vs_K64_solid_angle": err(ref[(32, True)], ref[(64, True)])}
         for v in ("exact", "relaxed"):
             for sc in ("cos", "exact"):
                 b = Projector(g, v, sc).project(x)
-                res[f"{v}/{sc}"] = err(b, ref[sc == "exact"])
+                for K in ks:
+                    res[f"{v}/{sc}_vs_K{K}"] = err(b, ref[(K, sc == "exact")])
         torch.cuda.synchronize()
         out["results"][name] = res
     print(json.dumps(out), flush=True)
@@ -607,6 +714,10 @@ def main():
         run_convs(args)
     elif args.paper_geometries:
         run_paper_geometries(args)
+    elif args.throughput:
+        run_throughput(args)
+    elif args.batch:
+        run_batch(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -54,7 +54,7 @@
 extern "C" {
 #endif
 
-#define KCT_VERSION 100
+#define KCT_VERSION 101
 
 typedef enum kct_status {
     KCT_OK = 0,
@@ -250,13 +250,16 @@ kct_status kct_project_static_device_error(int32_t *code, void *stream);
  *   d_b        device float32 [nviews][nv][nu], read only.
  *   d_x        device float32 [nz][ny][nx]: on entry the start x0 if warm_start != 0
  *              (ignored otherwise: the start is 0); on return the solution.
+ *   d_atb      optional device float32 [nz][ny][nx], read only: A^T b of this plan if the
+ *              caller already has it (a learned warm start computes it for its network input);
+ *              the solve then does one backprojection fewer. NULL: computed here.
  *   max_iter   >= 0.   tol >= 0 (0 runs max_iter steps).
  *   d_work     device scratch of at least kct_cgls_workspace_bytes(plan) bytes, 256-byte
  *              aligned; owned by the caller, contents on entry ignored.
  *   h_normal, h_data   optional host arrays of max_iter + 1 doubles (NULL to skip): entry k
  *              gets the normal residual and |b - A x_k| / |b| after k steps.
  *   report     optional: steps taken, whether tol was met, and the final residuals.
- * d_b and d_x must be 16-byte aligned and must not overlap d_work.
+ * d_b, d_x and d_atb must be 16-byte aligned and must not overlap d_work.
  * Synchronous: it reads the residuals from the device after every step (one 16-byte copy and
  * a stream synchronisation) and returns when the solve is done. Not for stream capture.
  */
@@ -269,8 +272,8 @@ typedef struct kct_cgls_report {
 
 size_t kct_cgls_workspace_bytes(const kct_plan *plan);
 
-kct_status kct_cgls(const kct_plan *plan, const float *d_b, float *d_x, int32_t warm_start, int32_t max_iter,
-                    double tol, void *d_work, size_t work_bytes, double *h_normal, double *h_data,
+kct_status kct_cgls(const kct_plan *plan, const float *d_b, float *d_x, const float *d_atb, int32_t warm_start,
+                    int32_t max_iter, double tol, void *d_work, size_t work_bytes, double *h_normal, double *h_data,
                     kct_cgls_report *report, void *stream);
 
 /* Static description of a status code. No counterpart in the paper (error reporting of

@@ -269,10 +269,16 @@ KCT_HD bool column_setup(const View& V, const Grid& G, int i, int j, Column& C) 
     int n0 = (int)floorf(umin + 0.5f), n1 = (int)floorf(umax + 0.5f);
     C.n_first = max(n0, 0);
     C.n_last = min(n1, G.nu - 1);
-    const double tcd = fma((double)V.wx + (double)V.wx_lo, fma((double)i, G.axd, G.x0d),
-                           fma((double)V.wy + (double)V.wy_lo, fma((double)j, G.ayd, G.y0d),
-                               (double)V.aw + (double)V.aw_lo));
-    C.da = f2_of(tcd * ((double)V.inv_agv + (double)V.inv_agv_lo));
+    // tc in two floats: the products w x exactly split by FMAs (x, y are exact voxel
+    // coordinates), summed with the low-order parts; then da = tc / |gv| = tc inv_agv
+    const float p1 = V.wx * x, e1 = fmaf(V.wx, x, -p1);
+    const float p2 = V.wy * y, e2 = fmaf(V.wy, y, -p2);
+    const float s1 = p1 + p2, z1 = s1 - p1, f1 = (p1 - (s1 - z1)) + (p2 - z1);
+    const float s2 = s1 + V.aw, z2 = s2 - s1, f2 = (s1 - (s2 - z2)) + (V.aw - z2);
+    const float tlo2 = e1 + e2 + f1 + f2 + tlo;
+    const float th = s2 + tlo2, tl = tlo2 - (th - s2);
+    const float dh = th * V.inv_agv;
+    C.da = F2{dh, fmaf(th, V.inv_agv, -dh) + fmaf(th, V.inv_agv_lo, tl * V.inv_agv)};
     return C.n_first <= C.n_last;
 }
 

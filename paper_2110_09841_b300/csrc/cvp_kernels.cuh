@@ -73,7 +73,7 @@ struct WarpSmem {
 // blocks stay small.
 struct WarpSmemRelaxed {
     Column C;
-    float4 fa[KCT_CB];             // A_n, t' of its centre of mass, 1/t_n, half the voxel's projected row extent
+    float4 fa[KCT_CB];             // A_n t_n / |gv|, t'_CM / t_n, 1/t_n, half the voxel's projected row extent
 };
 
 struct Tile {                      // detector window covered by a brick in one view
@@ -406,8 +406,22 @@ __device__ __forceinline__ void relaxed_voxels(const View& V, const Grid& G, con
                                                int kbase, int lane, const WarpSmemRelaxed* ws, Sink& sink,
                                                int* err) {
     const float az = G.az;
-    const F2 z0s = f2_of(G.z0d - ((double)V.sz + (double)V.sz_lo)), azF = f2_of(G.azd);
-    const float ida = __frcp_rn(C.da.hi);
+    // Row offset of a voxel centre at the column centre depth, vc = gv zeta / tc = sign(gv) zeta / da,
+    // and B = -cv - vc in two floats: the distance of row boundary m from the voxel centre's
+    // projection, m + B + vc delta (delta = t'_CM / t_n), is a small difference of large row
+    // coordinates, and thin slivers need it to float precision. Per column, B0 = -cv - vc of
+    // voxel 0 and dB = -sign(gv) az / da; voxel k has B = B0 + k dB.
+    F2 B0, dB;
+    {
+        const float ida = __fdividef(1.0f, C.da.hi);
+        const F2 z0s = f2_of(G.z0d - ((double)V.sz + (double)V.sz_lo)), azF = f2_of(G.azd);
+        const float q0 = z0s.hi * ida, q1 = (fmaf(-q0, C.da.hi, z0s.hi) + fmaf(-q0, C.da.lo, z0s.lo)) * ida;
+        const float r0 = azF.hi * ida, r1 = (fmaf(-r0, C.da.hi, azF.hi) + fmaf(-r0, C.da.lo, azF.lo)) * ida;
+        const float vch = V.sgv * q0;
+        const float bs = -V.cv - vch, bz = bs + V.cv;
+        B0 = F2{bs, ((-V.cv - (bs - bz)) + (-vch - bz)) - V.cv_lo - V.sgv * q1};
+        dB = F2{-V.sgv * r0, -V.sgv * r1};
+    }
     for (int pass = 0; pass < KPL; ++pass) {
         const int k = kbase + pass * 32 + lane;
         if (k >= G.nz) continue;
@@ -415,26 +429,18 @@ __device__ __forceinline__ void relaxed_voxels(const View& V, const Grid& G, con
         const float zc = fmaf((float)k, az, G.z0) - V.sz;
         const float iD2 = 1.0f / fmaf(C.tc, C.tc, fmaf(C.xc, C.xc, zc * zc));
         const float gz = V.gv * zc;
-        // Row offset of the voxel centre at the column centre depth, vc = gv zeta / tc =
-        // sign(gv) zeta / da, and B = -cv - vc in two floats: the distance of row boundary m from
-        // the voxel centre's projection, m + B + vc delta (delta = t'_CM / t_n), is a small
-        // difference of large row coordinates, and thin slivers need it to float precision.
-        const F2 zf = f2_axpy(z0s, (float)k, azF);
-        const float q0 = zf.hi * ida;                                       // zeta / da, then its residual
-        const float q1 = (fmaf(-q0, C.da.hi, zf.hi) + fmaf(-q0, C.da.lo, zf.lo)) * ida;
-        const float vch = V.sgv * q0, vcl = V.sgv * q1;
-        const float bs = -V.cv - vch, bz = bs + V.cv;
-        const float bl = ((-V.cv - (bs - bz)) + (-vch - bz)) - V.cv_lo - vcl;
+        const F2 Bk = f2_axpy(B0, (float)k, dB);
+        const float bs = Bk.hi, bl = Bk.lo, vch = -(bs + V.cv);
         for (int c = 0; c < ncol; ++c) {
-            const float4 fa = ws->fa[c];           // A_n, t'_CM, 1/t_n, hv
+            const float4 fa = ws->fa[c];           // A_n t_n / |gv|, t'_CM / t_n, 1/t_n, hv
             if (!(fa.x > 0.f)) continue;
             const float hv = fa.w;
             const float vn = fmaf(gz, fa.z, V.cv);
             const int m_first = max((int)floorf(vn - hv + 0.5f), 0);
             const int m_last = min((int)floorf(vn + hv + 0.5f), G.nv - 1);
             if (m_last - m_first + 2 > KCT_ROWS) { atomicOr(err, 1); continue; }
-            const float w = fa.x * (C.tc + fa.y) * V.inv_agv * iD2;
-            float e = ((float)m_first + bs) + fmaf(vch, fa.y * fa.z, bl);   // m_first - v_n
+            const float w = fa.x * iD2;
+            float e = ((float)m_first + bs) + fmaf(vch, fa.y, bl);   // m_first - v_n
             const int n = cstart + c;
             for (int m = m_first; m <= m_last; ++m, e += 1.0f) {
                 const float d = fminf(hv, e + 0.5f) - fmaxf(-hv, e - 0.5f);
@@ -462,8 +468,8 @@ __device__ __noinline__ void build_column_cut(const View* Vp, const Column* Cp, 
     }
     const float m1 = 0.5f * g.a, mt = g.t * (1.f / 6.f);
     const float tcm = m1 > 0.f ? mt / m1 : 0.f;            // t' of the centre of mass of H_n
-    const float itn = 1.0f / (C.tc + tcm);
-    ws->fa[c] = make_float4(m1, tcm, itn, 0.5f * az * fabsf(V.gv) * itn);
+    const float tn = C.tc + tcm, itn = 1.0f / tn;
+    ws->fa[c] = make_float4(m1 * tn * V.inv_agv, tcm * itn, itn, 0.5f * az * fabsf(V.gv) * itn);
 }
 
 // H_n for detector column n, near-exact variant: its vertices, the Green terms of its edges,

@@ -614,8 +614,8 @@ extern "C" {
 
 size_t kct_cgls_workspace_bytes(const kct_plan* p) { return p ? cgls_layout(p->grid).total : 0; }
 
-kct_status kct_cgls(const kct_plan* p, const float* d_b, float* d_x, int32_t warm_start, int32_t max_iter,
-                    double tol, void* d_work, size_t work_bytes, double* h_normal, double* h_data,
+kct_status kct_cgls(const kct_plan* p, const float* d_b, float* d_x, const float* d_atb, int32_t warm_start,
+                    int32_t max_iter, double tol, void* d_work, size_t work_bytes, double* h_normal, double* h_data,
                     kct_cgls_report* report, void* stream) {
     kct_status s = check_plan(p);
     if (s != KCT_OK) return s;
@@ -624,8 +624,8 @@ kct_status kct_cgls(const kct_plan* p, const float* d_b, float* d_x, int32_t war
     const Grid& G = p->grid;
     const CglsLayout L = cgls_layout(G);
     if (work_bytes < L.total) return fail(KCT_ERR_INVALID_ARG, "workspace smaller than kct_cgls_workspace_bytes");
-    if (((uintptr_t)d_work & 255) || ((uintptr_t)d_b & 15) || ((uintptr_t)d_x & 15))
-        return fail(KCT_ERR_INVALID_ARG, "d_work must be 256-byte and d_b, d_x 16-byte aligned");
+    if (((uintptr_t)d_work & 255) || ((uintptr_t)d_b & 15) || ((uintptr_t)d_x & 15) || ((uintptr_t)d_atb & 15))
+        return fail(KCT_ERR_INVALID_ARG, "d_work must be 256-byte and d_b, d_x, d_atb 16-byte aligned");
     if ((s = set_device(p)) != KCT_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     int sms = 0;
@@ -648,8 +648,13 @@ kct_status kct_cgls(const kct_plan* p, const float* d_b, float* d_x, int32_t war
     kct::sumsq_kernel<<<nb, T, 0, st>>>(d_b, nproj, part_rr);
     kct::store_sum_kernel<<<1, T, 0, st>>>(part_rr, nb, &sc->bb2);
     if (warm_start) {
-        if ((s = backproject_impl(p, d_b, sv, 1, 0, st)) != KCT_OK) return s;
-        kct::sumsq_kernel<<<nb, T, 0, st>>>(sv, nvol, part_ss);
+        // |A^T b|, the denominator of the stopping rule, from the caller's A^T b if given
+        if (d_atb) {
+            kct::sumsq_kernel<<<nb, T, 0, st>>>(d_atb, nvol, part_ss);
+        } else {
+            if ((s = backproject_impl(p, d_b, sv, 1, 0, st)) != KCT_OK) return s;
+            kct::sumsq_kernel<<<nb, T, 0, st>>>(sv, nvol, part_ss);
+        }
         kct::store_sum_kernel<<<1, T, 0, st>>>(part_ss, nb, &sc->atb2);
         if ((s = project_impl(p, d_x, q, 1, 0, st)) != KCT_OK) return s;
         kct::residual_kernel<<<nb, T, 0, st>>>(d_b, q, r, nproj, part_rr);
@@ -658,8 +663,9 @@ kct_status kct_cgls(const kct_plan* p, const float* d_b, float* d_x, int32_t war
     } else {
         e = cudaMemsetAsync(d_x, 0, sizeof(float) * nvol, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(r, d_b, sizeof(float) * nproj, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess && d_atb) e = cudaMemcpyAsync(sv, d_atb, sizeof(float) * nvol, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return cuda_fail(e, "CGLS start");
-        if ((s = backproject_impl(p, r, sv, 1, 0, st)) != KCT_OK) return s;
+        if (!d_atb && (s = backproject_impl(p, r, sv, 1, 0, st)) != KCT_OK) return s;
         kct::sumsq_kernel<<<nb, T, 0, st>>>(sv, nvol, part_ss);
         kct::store_sum_kernel<<<1, T, 0, st>>>(part_ss, nb, &sc->atb2);
     }

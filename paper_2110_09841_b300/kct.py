@@ -104,7 +104,7 @@ def load(path: str | None = None):
         lib.kct_plan_get_view_chunk.restype = I
         lib.kct_cgls_workspace_bytes.argtypes = [V]
         lib.kct_cgls_workspace_bytes.restype = ctypes.c_size_t
-        lib.kct_cgls.argtypes = [V, V, V, I32, I32, ctypes.c_double, V, ctypes.c_size_t, V, V,
+        lib.kct_cgls.argtypes = [V, V, V, V, I32, I32, ctypes.c_double, V, ctypes.c_size_t, V, V,
                                  ctypes.POINTER(CglsReport), V]
         lib.kct_cgls.restype = I
         _lib = lib
@@ -259,9 +259,10 @@ class Projector:
 
         return torch.empty(int(self.lib.kct_cgls_workspace_bytes(self._h)), dtype=torch.uint8, device="cuda")
 
-    def cgls(self, b, x0=None, max_iter=100, tol=1e-3, out=None, workspace=None, stream=None):
+    def cgls(self, b, x0=None, max_iter=100, tol=1e-3, out=None, workspace=None, atb=None, stream=None):
         """CGLS for min |b - A x| (kct_cgls): from x0 (warm start) or from 0, until the
         normal-equation residual |A^T(b - A x)| / |A^T b| <= tol or max_iter steps.
+        atb: optional A^T b already at hand (saves the solve one backprojection).
         Returns (x, info) with info = dict(iterations, converged, normal, data); normal and
         data are the residual histories (entry k after k steps)."""
         import torch
@@ -280,7 +281,8 @@ class Projector:
         hn = np.zeros(max_iter + 1)
         hd = np.zeros(max_iter + 1)
         rep = CglsReport()
-        _check(self.lib.kct_cgls(self._h, bp, xp, int(x0 is not None), int(max_iter), float(tol),
+        ap = _dev_ptr(atb, g.vol_shape, "atb") if atb is not None else None
+        _check(self.lib.kct_cgls(self._h, bp, xp, ap, int(x0 is not None), int(max_iter), float(tol),
                                  ctypes.c_void_p(workspace.data_ptr()), int(workspace.numel()),
                                  hn.ctypes.data_as(ctypes.c_void_p), hd.ctypes.data_as(ctypes.c_void_p),
                                  ctypes.byref(rep), _stream_handle(stream)))

@@ -49,7 +49,7 @@ def test_conv_library_exports_every_declared_symbol():
 
 
 def test_version_and_status_strings(lib):
-    assert lib.kct_version() == 100
+    assert lib.kct_version() == 101
     for s in range(7):
         assert lib.kct_status_string(s).decode()
     assert lib.kct_status_string(99).decode() == "unknown status"
@@ -86,7 +86,7 @@ def test_rejects_invalid_arguments(lib):
     assert lib.kct_plan_set_view_chunk(None, 4) == 1
     assert lib.kct_plan_autotune(None, None, None, None, None, None) == 1
     assert lib.kct_cgls_workspace_bytes(None) == 0
-    assert lib.kct_cgls(None, None, None, 0, 1, 1e-3, None, 0, None, None, None, None) == 1
+    assert lib.kct_cgls(None, None, None, None, 0, 1, 1e-3, None, 0, None, None, None, None) == 1
     assert lib.kct_siddon_project(None, None, None, 8, 0, None) == 1
     assert lib.kct_plan_get_view_chunk(None, None) == 1
 

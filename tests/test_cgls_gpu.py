@@ -101,10 +101,27 @@ def test_rejects_bad_workspace_and_alignment():
     assert e.value.status == 1
     ws = A.cgls_workspace()
     buf = torch.zeros(g.nx * g.ny * g.nz + 1, device="cuda")
-    rc = A.lib.kct_cgls(A.handle, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(buf.data_ptr() + 4), 0, 2,
+    rc = A.lib.kct_cgls(A.handle, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(buf.data_ptr() + 4), None, 0, 2,
                         1e-3, ctypes.c_void_p(ws.data_ptr()), ws.numel(), None, None, None,
                         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == 1
+
+
+@pytest.mark.parametrize("warm", [False, True])
+def test_precomputed_atb_gives_the_same_solve(warm):
+    """Passing A^T b (which a learned warm start already computes) skips one backprojection
+    and changes nothing else: the same iterates and residual histories."""
+    g = small()
+    A = Projector(g, "relaxed", "cos")
+    truth = phantom(g, 5).cuda()
+    b = A.project(truth)
+    x0 = 0.5 * truth if warm else None
+    x1, i1 = A.cgls(b, x0=x0, max_iter=6, tol=0.0)
+    x2, i2 = A.cgls(b, x0=x0, max_iter=6, tol=0.0, atb=A.backproject(b))
+    assert i1["iterations"] == i2["iterations"] == 6
+    np.testing.assert_allclose(i2["normal"], i1["normal"], rtol=1e-5)
+    np.testing.assert_allclose(i2["data"], i1["data"], rtol=1e-5)
+    assert float((x1 - x2).abs().max()) <= 1e-5 * float(x1.abs().max())
 
 
 def test_zero_data_gives_zero():

@@ -121,6 +121,37 @@ def test_captured_graph_replays():
 
 
 @pytest.mark.parametrize("vname", ["exact", "relaxed"])
+def test_batched_calls_captured_in_a_graph(vname):
+    """A batch of perfusion-like frames projected and backprojected by one batched launch each,
+    captured once in a CUDA graph and replayed on new frames (the configuration of the batched
+    benchmark, at a small size): replays equal eager batched calls."""
+    g = inputs.make_geometry((24, 24, 20), (1.0, 1.0, 1.0), (48, 40), (0.8, 0.8), 20, 750.0, 1200.0, 200.0)
+    A = Projector(g, vname, "cos")
+    A.autotune(inputs.perfusion_frames(g, 40, frames=1, device="cuda")[0].contiguous())
+    frames = torch.zeros((4,) + g.vol_shape, device="cuda")
+    proj = torch.empty((4,) + g.proj_shape, device="cuda")
+    back = torch.empty((4,) + g.vol_shape, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        A.project_batch(frames, out=proj)
+        A.backproject_batch(proj, out=back)
+    torch.cuda.current_stream().wait_stream(s)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        A.project_batch(frames, out=proj)
+        A.backproject_batch(proj, out=back)
+    for seed in (41, 42):
+        frames.copy_(inputs.perfusion_frames(g, seed, frames=4, device="cuda"))
+        graph.replay()
+        torch.cuda.synchronize()
+        rp = A.project_batch(frames)
+        torch.testing.assert_close(proj, rp, rtol=1e-5, atol=1e-6 * float(rp.abs().max()))
+        torch.testing.assert_close(back, A.backproject_batch(proj), rtol=0, atol=0)
+    assert A.device_error() == 0
+
+
+@pytest.mark.parametrize("vname", ["exact", "relaxed"])
 def test_autotuned_chunk_gives_the_same_projection(vname):
     g = inputs.workload_geometry("cvp32")
     x = inputs.workload_phantom("cvp32").cuda()
