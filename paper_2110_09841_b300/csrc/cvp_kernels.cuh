@@ -154,6 +154,17 @@ __device__ __forceinline__ float pair_weight(float pv, float pq, float D2) {
     return __fdividef(pv * pv, fmaf(pv, D2, 2.f * pq));
 }
 
+// bit index of floor(x) / ceil(x) for a plane index bound x, clamped to [-1, 32]
+__device__ __forceinline__ int floor_bit(float x) { return (int)floorf(fminf(fmaxf(x, -1.f), 32.f)); }
+__device__ __forceinline__ int ceil_bit(float x) { return (int)ceilf(fminf(fmaxf(x, -1.f), 32.f)); }
+
+// bits lo .. hi of a 32-bit word (lo, hi clamped to 0 .. 31; empty if lo > hi)
+__device__ __forceinline__ unsigned range_bits(int lo, int hi) {
+    lo = max(lo, 0);
+    hi = min(hi, 31);
+    return lo > hi ? 0u : ((2u << hi) - (1u << lo));
+}
+
 // Near-exact pairs of voxels kbase + lane + 32 p of the warp's column with detector
 // columns n = cstart .. cstart + ncol - 1, one detector column at a time. Each pair (n, m)
 // is the integral over H_n of the height between the two row planes of row m. When both
@@ -165,7 +176,7 @@ __device__ __forceinline__ float pair_weight(float pv, float pq, float D2) {
 template <class Sink>
 __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const Column& C, int cstart, int ncol,
                                              int kbase, int lane, WarpSmem* ws, Sink& sink, int* err) {
-    const float az = G.az;
+    const float az = G.az, agv = fabsf(V.gv);
     const float dp0 = C.tc * V.inv_agv, dp1 = V.inv_agv;   // change of p0, p1 from one row boundary to the next
     const float vtiny = 1e-9f * G.ax * G.ay * az;
     // Height offset of row boundary m - 1/2 over the centre of voxel k at the column centre depth,
@@ -220,17 +231,20 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
             const float off0 = row_offset(k, m_first[p]);
             off0p[p] = off0;
             const float p1_0 = ((float)m_first[p] - 0.5f - V.cv) * V.inv_agv;
-            // classes of the boundaries: 0 / az for planes outside the voxel, crossing mask
-            unsigned cr = 0u, ze = 0u, fu = 0u;
-#pragma unroll 1
-            for (int b = 0; b <= R[p]; ++b) {
-                const float p0 = fmaf(0.5f, az, fmaf((float)b, dp0, off0)), p1 = fmaf((float)b, dp1, p1_0);
-                const float h0 = fmaf(p1, tlo, p0), h1 = fmaf(p1, thi, p0);
-                const float hmin = fminf(h0, h1), hmax = fmaxf(h0, h1);
-                if (hmax <= 0.f) ze |= 1u << b;
-                else if (hmin >= az) fu |= 1u << b;
-                else if (hmin < 0.f || hmax > az) cr |= 1u << b;
-            }
+            // classes of the boundaries b = 0 .. R (0 / az for planes under / over the voxel, inside,
+            // crossing a face), in closed form: at the two ends of the depth range of H_n the height
+            // of plane b is H0 + b S0 and H1 + b S1 with S0, S1 = (tc + t') / |gv| > 0, so the planes
+            // under the voxel, over it and inside it are three ranges of b, and the rest cross a face
+            const float iS0 = agv * fr.x, iS1 = agv * fr.y;            // 1 / S0, 1 / S1
+            const float c0 = fmaf(0.5f, az, off0);
+            const float H0 = fmaf(p1_0, tlo, c0), H1 = fmaf(p1_0, thi, c0);
+            const float n0 = -H0 * iS0, n1 = -H1 * iS1;                 // b where an end height is 0
+            const float a0 = (az - H0) * iS0, a1 = (az - H1) * iS1;     // ... where it is az
+            const unsigned all = (2u << R[p]) - 1u;
+            const unsigned ze = range_bits(-1, floor_bit(fminf(n0, n1))) & all;
+            const unsigned fu = range_bits(ceil_bit(fmaxf(a0, a1)), 32) & all & ~ze;
+            const unsigned in = range_bits(ceil_bit(fmaxf(n0, n1)), floor_bit(fminf(a0, a1))) & all & ~ze & ~fu;
+            const unsigned cr = all & ~(ze | fu | in);
             cross[p] = cr;
             zero[p] = ze;
             full[p] = fu;
