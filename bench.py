@@ -36,25 +36,26 @@ UNIT = "Gvoxel·views/s"
 #   warp_per_vv  warp instructions issued per voxel-view, simt: active lanes per instruction / 32,
 #   dram_8       DRAM bytes read + written by that 8-view launch.
 # A full 496-view launch processes 62x the voxel-views; the forward kernel re-reads the
-# volume once per chunk of 16 views and adds one projection per view, the adjoint reads one
-# projection tile per view and writes the volume once, so traffic is scaled as below.
+# volume once per chunk of views (the capture's 8 views are one chunk) and adds one projection
+# per view, the adjoint reads one projection tile per view and writes the volume once, so
+# traffic is scaled as below.
 NCU = {
-    "exact project": {"flop_per_vv": 964.4, "warp_per_vv": 112.4, "simt": 0.61,
-                      "dram_read_8": 5.7736e8, "dram_write_8": 3.0488e7},
-    "exact backproject": {"flop_per_vv": 1034.8, "warp_per_vv": 117.3, "simt": 0.62,
-                          "dram_read_8": 5.9742e7, "dram_write_8": 4.9289e8},
-    "relaxed project": {"flop_per_vv": 159.0, "warp_per_vv": 25.2, "simt": 0.64,
-                        "dram_read_8": 5.7725e8, "dram_write_8": 3.1695e7},
-    "relaxed backproject": {"flop_per_vv": 196.0, "warp_per_vv": 35.0, "simt": 0.60,
-                            "dram_read_8": 5.6709e7, "dram_write_8": 4.9702e8},
+    "exact project": {"flop_per_vv": 908.4, "warp_per_vv": 105.6, "simt": 0.60,
+                      "dram_read_8": 5.78e8, "dram_write_8": 3.11e7},
+    "exact backproject": {"flop_per_vv": 980.0, "warp_per_vv": 111.0, "simt": 0.62,
+                          "dram_read_8": 6.06e7, "dram_write_8": 4.94e8},
+    "relaxed project": {"flop_per_vv": 187.0, "warp_per_vv": 26.6, "simt": 0.66,
+                        "dram_read_8": 5.77e8, "dram_write_8": 3.26e7},
+    "relaxed backproject": {"flop_per_vv": 232.1, "warp_per_vv": 36.3, "simt": 0.61,
+                            "dram_read_8": 5.35e7, "dram_write_8": 4.98e8},
 }
 
 
-def full_launch_traffic(name: str, nviews: int) -> float:
+def full_launch_traffic(name: str, nviews: int, chunk: int = 16) -> float:
     c = NCU[name]
     if name.endswith("backproject"):      # per-view tile reads scale, the volume write does not
         return c["dram_read_8"] * nviews / 8 + c["dram_write_8"]
-    chunks = (nviews + 15) // 16           # volume re-read per 16-view chunk, writes per view
+    chunks = (nviews + chunk - 1) // chunk  # volume re-read per chunk of views, writes per view
     return c["dram_read_8"] * chunks + c["dram_write_8"] * nviews / 8
 
 
@@ -73,6 +74,7 @@ def parse(argv=None):
     ap.add_argument("--scaling", default="cos", choices=["cos", "exact"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cgls", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default forward view chunk (16)")
     ap.add_argument("--accuracy", action="store_true",
                     help="compare both variants and scalings with supersampled ray integration (K = 32, 64) and exit")
     ap.add_argument("--convs", action="store_true",
@@ -338,6 +340,14 @@ def run_kct(args):
     y = inputs.uniform_projections(geom.proj_shape, 2024, device=dev)
     variants = ("exact", "relaxed")
     ops = {v: Projector(geom, v, args.scaling) for v in variants}
+    # the forward view chunk picked by the plan's own autotuner (kct_plan_autotune), before any
+    # timing; the chunks are reported in the JSON line
+    tuned = {}
+    if not args.no_autotune:
+        scratch = torch.empty(geom.proj_shape, dtype=torch.float32, device=dev)
+        for v in variants:
+            tuned[v] = ops[v].autotune(x, scratch)[0]
+        del scratch
     b = {v: torch.empty(geom.proj_shape, dtype=torch.float32, device=dev) for v in variants}
     xb = {v: torch.empty(geom.vol_shape, dtype=torch.float32, device=dev) for v in variants}
     stream = torch.cuda.current_stream()
@@ -388,6 +398,7 @@ def run_kct(args):
     value = aggregate_gvv_s(units_per_step, args.steps, total_ms, world)
     for v in variants:
         p = per[v]
+        p["view_chunk"] = ops[v].view_chunk
         p["p_bp_gvv_s"] = geom.voxel_views / ((p["project_ms"] + p["backproject_ms"]) / 1e3) / 1e9
         p["nnz_pairs"] = ops[v].count_pairs()
         p["nnz_pairs_per_s_p_bp"] = 2 * p["nnz_pairs"] / ((p["project_ms"] + p["backproject_ms"]) / 1e3)
@@ -445,7 +456,7 @@ def run_kct(args):
     name = f"{dom_v} {dom_k[:-3]}"
     flop_vv = NCU[name]["flop_per_vv"] if args.workload == WORKLOAD else None
     achieved = (flop_vv * geom.voxel_views / (dom_ms / 1e3) / 1e12) if flop_vv else None
-    traffic = full_launch_traffic(name, geom.nviews) if args.workload == WORKLOAD else None
+    traffic = full_launch_traffic(name, geom.nviews, ops[dom_v].view_chunk) if args.workload == WORKLOAD else None
     fp32_probe = probe_fp32_tflops()
     # the same kernel against the instruction-issue limit (4 warp instructions per SM and cycle)
     wpv = NCU[name]["warp_per_vv"] if args.workload == WORKLOAD else None
