@@ -150,6 +150,16 @@ KCT_HD void g_lin(float az, float p0, float p1, float zs, float f1, float ft, fl
     gq = fmaf(zs, fmaf(0.5f, Sh2, -0.5f * az * Vg), Sl);
 }
 
+// g_lin with paired FP32 instructions (two independent FMAs per issue)
+__device__ __forceinline__ void g_lin2(float az, float p0, float p1, float zs, float f1, float ft, float ftt, float fl,
+                                       float flt, float& gv, float& gq) {
+    const float2 vs = __ffma2_rn(make_float2(p0, p0), make_float2(f1, fl), __fmul2_rn(make_float2(p1, p1), make_float2(ft, flt)));
+    const float2 sq = __fmul2_rn(make_float2(p0, p1), make_float2(p0, p1));
+    const float Sh2 = fmaf(sq.x, f1, fmaf(2.f * p0 * p1, ft, sq.y * ftt));
+    gv = vs.x;
+    gq = fmaf(zs, fmaf(0.5f, Sh2, -0.5f * az * vs.x), vs.y);
+}
+
 __device__ __forceinline__ float pair_weight(float pv, float pq, float D2) {
     return __fdividef(pv * pv, fmaf(pv, D2, 2.f * pq));
 }
@@ -344,6 +354,9 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
                     const float zs = zc * V.sgv;
                     const float D2 = fmaf(C.tc, C.tc, fmaf(C.xc, C.xc, zc * zc));
                     const float p1_0 = ((float)m_first[p] - 0.5f - V.cv) * V.inv_agv;
+                    // row centre heights s0 = tc (m - v_c) / |gv|, s1 = (m - cv) / |gv| are m dp0 + sbase.x, m dp1 + sbase.y
+                    const float2 sbase = make_float2(C.tc * (-fmaf(V.gv, bc, V.cv)) * V.inv_agv, -V.cv * V.inv_agv);
+                    const float2 zd = make_float2(zs * dp0, zs * dp1);
                     const int rb = (R[p] + 1) >> 1;
                     const unsigned mbot = cross[p] & ((2u << rb) - 1u), mtop = cross[p] & ~((1u << rb) - 1u);
                     const int nbot = __popc(mbot);
@@ -359,11 +372,13 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
                         if (!((cross[p] | zero[p] | full[p]) & (bl | bh))) {
                             carry = false;
                             // both planes inside: height dp0 + dp1 t' centred at s0 + s1 t'
-                            const float s0 = C.tc * (-fmaf(V.gv, bc, V.cv - (float)m)) * V.inv_agv;
-                            const float s1 = ((float)m - V.cv) * V.inv_agv;
-                            const float a0 = zs * dp0 * s0, a1 = zs * fmaf(dp0, s1, dp1 * s0), a2 = zs * dp1 * s1;
-                            pv = fmaf(dp0, fa.x, dp1 * fa.y);
-                            pq = fmaf(dp0, fa.w, fmaf(dp1, fb.x, fmaf(a0, fa.x, fmaf(a1, fa.y, a2 * fa.z))));
+                            const float2 ss = __ffma2_rn(make_float2((float)m, (float)m), make_float2(dp0, dp1), sbase);
+                            const float2 a02 = __fmul2_rn(zd, ss);                  // zs dp0 s0, zs dp1 s1
+                            const float a1 = fmaf(zd.x, ss.y, zd.y * ss.x);
+                            const float2 vq = __ffma2_rn(make_float2(dp0, dp0), make_float2(fa.x, fa.w),
+                                                         __fmul2_rn(make_float2(dp1, dp1), make_float2(fa.y, fb.x)));
+                            pv = vq.x;
+                            pq = fmaf(a02.x, fa.x, fmaf(a1, fa.y, fmaf(a02.y, fa.z, vq.y)));
                         } else {
                             const bool top = r >= rb;
                             float g[2][2];
@@ -375,13 +390,15 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
                                 if (h == 0 && reuse) continue;
                                 const int b = r + h;
                                 const unsigned bit = 1u << b;
-                                float p0 = fmaf(0.5f, az, fmaf((float)b, dp0, off0p[p])), p1 = fmaf((float)b, dp1, p1_0);
+                                const float2 pp = __ffma2_rn(make_float2((float)b, (float)b), make_float2(dp0, dp1),
+                                                             make_float2(off0p[p], p1_0));
+                                float p0 = pp.x + 0.5f * az, p1 = pp.y;
                                 if (zero[p] & bit) { p0 = 0.f; p1 = 0.f; }
                                 if (full[p] & bit) { p0 = az; p1 = 0.f; }
                                 // the linear form in the row's frame is evaluated by every lane (no
                                 // divergence on the frame); crossing planes then take the queued result
-                                g_lin(az, top ? az - p0 : p0, top ? -p1 : p1, top ? -zs : zs, fa.x, fa.y, fa.z, fa.w, fb.x,
-                                      g[h][0], g[h][1]);
+                                g_lin2(az, top ? az - p0 : p0, top ? -p1 : p1, top ? -zs : zs, fa.x, fa.y, fa.z, fa.w, fb.x,
+                                       g[h][0], g[h][1]);
                                 if (cross[p] & bit) {
                                     const int q = top ? ep + nbot + __popc(mtop & (bit - 1u)) : ep + __popc(mbot & (bit - 1u));
                                     g[h][0] = ws->res_v[q];
