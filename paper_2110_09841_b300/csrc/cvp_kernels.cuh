@@ -164,6 +164,22 @@ __device__ __forceinline__ float pair_weight(float pv, float pq, float D2) {
     return __fdividef(pv * pv, fmaf(pv, D2, 2.f * pq));
 }
 
+// Per-column constants of the row geometry in two floats: the voxel centre k projects at row
+// cv + vc_k at the column centre depth, vc_k = gv zeta_k / tc = sign(gv) zeta_k / da; with
+// B_k = -cv - vc_k = B0 + k dB, the distance of row boundary m - 1/2 from that projection is
+// (m - 1/2) + B_k: a small difference of large row coordinates, which thin slivers need to
+// float precision (the plain float sum loses up to ulp(cv + vc) rows).
+__device__ __forceinline__ void row_frame(const View& V, const Grid& G, const Column& C, F2& B0, F2& dB) {
+    const float ida = __fdividef(1.0f, C.da.hi);
+    const F2 z0s = f2_of(G.z0d - ((double)V.sz + (double)V.sz_lo)), azF = f2_of(G.azd);
+    const float q0 = z0s.hi * ida, q1 = (fmaf(-q0, C.da.hi, z0s.hi) + fmaf(-q0, C.da.lo, z0s.lo)) * ida;
+    const float r0 = azF.hi * ida, r1 = (fmaf(-r0, C.da.hi, azF.hi) + fmaf(-r0, C.da.lo, azF.lo)) * ida;
+    const float vch = V.sgv * q0;
+    const float bs = -V.cv - vch, bz = bs + V.cv;
+    B0 = F2{bs, ((-V.cv - (bs - bz)) + (-vch - bz)) - V.cv_lo - V.sgv * q1};
+    dB = F2{-V.sgv * r0, -V.sgv * r1};
+}
+
 // bit index of floor(x) / ceil(x) for a plane index bound x, clamped to [-1, 32]
 __device__ __forceinline__ int floor_bit(float x) { return (int)floorf(fminf(fmaxf(x, -1.f), 32.f)); }
 __device__ __forceinline__ int ceil_bit(float x) { return (int)ceilf(fminf(fmaxf(x, -1.f), 32.f)); }
@@ -190,19 +206,14 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
     const float dp0 = C.tc * V.inv_agv, dp1 = V.inv_agv;   // change of p0, p1 from one row boundary to the next
     const float vtiny = 1e-9f * G.ax * G.ay * az;
     // Height offset of row boundary m - 1/2 over the centre of voxel k at the column centre depth,
-    // tc (m - 1/2 - cv) / |gv| - sign(gv) zeta_k, in two-float arithmetic: its two terms are large
-    // and nearly cancel, and thin slivers (a plane close to a face) need the difference to float
-    // precision. A plane b rows higher is then az/2 + b dp0 + offset (small terms, plain float).
-    const F2 z0s = f2_of(G.z0d - ((double)V.sz + (double)V.sz_lo)), azF = f2_of(G.azd);
+    // tc (m - 1/2 - v_c) / |gv| = ((m - 1/2) + B_k) da (row_frame): the row distance is formed in
+    // two floats and is small, so the offset keeps float precision; a plane b rows higher is
+    // then az/2 + b dp0 + offset (small terms, plain float).
+    F2 B0, dB;
+    row_frame(V, G, C, B0, dB);
     auto row_offset = [&](int k, int m) -> float {
-        const F2 zc = f2_axpy(z0s, (float)k, azF);
-        const F2 sg = V.sgv > 0.f ? zc : F2{-zc.hi, -zc.lo};
-        // (m - 1/2 - cv) da: m - 1/2 is exact, cv and da carry low-order parts (two-sum, two-product)
-        const float a = (float)m - 0.5f, s = a - V.cv, bb = s - a;
-        const float dvl = ((a - (s - bb)) + (-V.cv - bb)) - V.cv_lo;
-        const float ph = s * C.da.hi;
-        const F2 a0 = F2{ph, fmaf(s, C.da.hi, -ph) + fmaf(s, C.da.lo, dvl * C.da.hi)};
-        return f2_diff(a0, sg);
+        const F2 Bk = f2_axpy(B0, (float)k, dB);
+        return ((((float)m - 0.5f) + Bk.hi) + Bk.lo) * C.da.hi;
     };
     // the lane's voxels kbase + lane + 32 p; their crossing planes share one queue round
 #pragma unroll
@@ -437,22 +448,11 @@ __device__ __forceinline__ void relaxed_voxels(const View& V, const Grid& G, con
                                                int kbase, int lane, const WarpSmemRelaxed* ws, Sink& sink,
                                                int* err) {
     const float az = G.az;
-    // Row offset of a voxel centre at the column centre depth, vc = gv zeta / tc = sign(gv) zeta / da,
-    // and B = -cv - vc in two floats: the distance of row boundary m from the voxel centre's
-    // projection, m + B + vc delta (delta = t'_CM / t_n), is a small difference of large row
-    // coordinates, and thin slivers need it to float precision. Per column, B0 = -cv - vc of
-    // voxel 0 and dB = -sign(gv) az / da; voxel k has B = B0 + k dB.
+    // distance of row boundary m from the voxel centre's projection at the column centre depth,
+    // (m + B_k) with B_k = -cv - vc_k in two floats (row_frame); at the centroid depth t_n of H_n
+    // it is m + B_k + vc_k delta, delta = t'_CM / t_n
     F2 B0, dB;
-    {
-        const float ida = __fdividef(1.0f, C.da.hi);
-        const F2 z0s = f2_of(G.z0d - ((double)V.sz + (double)V.sz_lo)), azF = f2_of(G.azd);
-        const float q0 = z0s.hi * ida, q1 = (fmaf(-q0, C.da.hi, z0s.hi) + fmaf(-q0, C.da.lo, z0s.lo)) * ida;
-        const float r0 = azF.hi * ida, r1 = (fmaf(-r0, C.da.hi, azF.hi) + fmaf(-r0, C.da.lo, azF.lo)) * ida;
-        const float vch = V.sgv * q0;
-        const float bs = -V.cv - vch, bz = bs + V.cv;
-        B0 = F2{bs, ((-V.cv - (bs - bz)) + (-vch - bz)) - V.cv_lo - V.sgv * q1};
-        dB = F2{-V.sgv * r0, -V.sgv * r1};
-    }
+    row_frame(V, G, C, B0, dB);
     for (int pass = 0; pass < KPL; ++pass) {
         const int k = kbase + pass * 32 + lane;
         if (k >= G.nz) continue;
