@@ -32,7 +32,8 @@ UNIT = "Gvoxel·views/s"
 
 # Per-kernel counts from one ncu capture of each projector kernel on the benchmark geometry
 # restricted to 8 of its views (python bench.py --profile-case cvp512 --views 8 ...):
-#   flop_per_vv  FP32 operations (thread-level FADD + FMUL + 2 FFMA) per voxel-view,
+#   flop_per_vv  FP32 operations (thread-level FADD + FMUL + 2 FFMA, the paired FADD2 / FMUL2 /
+#                FFMA2 counted as 2 / 2 / 4) per voxel-view,
 #   warp_per_vv  warp instructions issued per voxel-view, simt: active lanes per instruction / 32,
 #   dram_8       DRAM bytes read + written by that 8-view launch.
 # A full 496-view launch processes 62x the voxel-views; the forward kernel re-reads the
@@ -40,14 +41,14 @@ UNIT = "Gvoxel·views/s"
 # per view, the adjoint reads one projection tile per view and writes the volume once, so
 # traffic is scaled as below.
 NCU = {
-    "exact project": {"flop_per_vv": 908.4, "warp_per_vv": 105.6, "simt": 0.60,
-                      "dram_read_8": 5.78e8, "dram_write_8": 3.11e7},
-    "exact backproject": {"flop_per_vv": 980.0, "warp_per_vv": 111.0, "simt": 0.62,
-                          "dram_read_8": 6.06e7, "dram_write_8": 4.94e8},
+    "exact project": {"flop_per_vv": 868.4, "warp_per_vv": 103.6, "simt": 0.60,
+                      "dram_read_8": 5.77e8, "dram_write_8": 3.06e7},
+    "exact backproject": {"flop_per_vv": 937.8, "warp_per_vv": 108.9, "simt": 0.62,
+                          "dram_read_8": 5.72e7, "dram_write_8": 4.94e8},
     "relaxed project": {"flop_per_vv": 187.0, "warp_per_vv": 26.6, "simt": 0.66,
-                        "dram_read_8": 5.77e8, "dram_write_8": 3.26e7},
+                        "dram_read_8": 5.76e8, "dram_write_8": 3.26e7},
     "relaxed backproject": {"flop_per_vv": 232.1, "warp_per_vv": 36.3, "simt": 0.61,
-                            "dram_read_8": 5.35e7, "dram_write_8": 4.98e8},
+                            "dram_read_8": 5.28e7, "dram_write_8": 4.97e8},
 }
 
 
