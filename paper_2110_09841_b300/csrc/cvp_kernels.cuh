@@ -361,39 +361,25 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
                 for (int p = 0; p < KPL; ++p) {
                     const int k = kbase + p * 32 + lane;
                     const float zc = fmaf((float)k, az, G.z0) - V.sz;
-                    const float bc = zc * C.itc;
                     const float zs = zc * V.sgv;
                     const float D2 = fmaf(C.tc, C.tc, fmaf(C.xc, C.xc, zc * zc));
                     const float p1_0 = ((float)m_first[p] - 0.5f - V.cv) * V.inv_agv;
-                    // row centre heights s0 = tc (m - v_c) / |gv|, s1 = (m - cv) / |gv| are m dp0 + sbase.x, m dp1 + sbase.y
-                    const float2 sbase = make_float2(C.tc * (-fmaf(V.gv, bc, V.cv)) * V.inv_agv, -V.cv * V.inv_agv);
-                    const float2 zd = make_float2(zs * dp0, zs * dp1);
                     const int rb = (R[p] + 1) >> 1;
                     const unsigned mbot = cross[p] & ((2u << rb) - 1u), mtop = cross[p] & ~((1u << rb) - 1u);
                     const int nbot = __popc(mbot);
-                    // region value of the previous row's upper plane, reused as this row's lower
-                    // plane when both rows use the same frame
+                    // Every row is the difference of its two planes' region values in the row's frame
+                    // (bottom for r < rb, top after), so all lanes take the same path whatever the
+                    // planes' classes; the upper plane's value is carried to the next row, whose
+                    // lower plane it is (recomputed where the frame changes).
                     float carry_v = 0.f, carry_q = 0.f;
-                    bool carry = false;
 #pragma unroll 1
                     for (int r = 0; r < R[p]; ++r) {
                         const int m = m_first[p] + r;
-                        const unsigned bl = 1u << r, bh = 2u << r;
                         float pv, pq;
-                        if (!((cross[p] | zero[p] | full[p]) & (bl | bh))) {
-                            carry = false;
-                            // both planes inside: height dp0 + dp1 t' centred at s0 + s1 t'
-                            const float2 ss = __ffma2_rn(make_float2((float)m, (float)m), make_float2(dp0, dp1), sbase);
-                            const float2 a02 = __fmul2_rn(zd, ss);                  // zs dp0 s0, zs dp1 s1
-                            const float a1 = fmaf(zd.x, ss.y, zd.y * ss.x);
-                            const float2 vq = __ffma2_rn(make_float2(dp0, dp0), make_float2(fa.x, fa.w),
-                                                         __fmul2_rn(make_float2(dp1, dp1), make_float2(fa.y, fb.x)));
-                            pv = vq.x;
-                            pq = fmaf(a02.x, fa.x, fmaf(a1, fa.y, fmaf(a02.y, fa.z, vq.y)));
-                        } else {
+                        {
                             const bool top = r >= rb;
                             float g[2][2];
-                            const bool reuse = carry && r != rb;
+                            const bool reuse = r > 0 && r != rb;
                             g[0][0] = carry_v;
                             g[0][1] = carry_q;
 #pragma unroll
@@ -406,8 +392,6 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
                                 float p0 = pp.x + 0.5f * az, p1 = pp.y;
                                 if (zero[p] & bit) { p0 = 0.f; p1 = 0.f; }
                                 if (full[p] & bit) { p0 = az; p1 = 0.f; }
-                                // the linear form in the row's frame is evaluated by every lane (no
-                                // divergence on the frame); crossing planes then take the queued result
                                 g_lin2(az, top ? az - p0 : p0, top ? -p1 : p1, top ? -zs : zs, fa.x, fa.y, fa.z, fa.w, fb.x,
                                        g[h][0], g[h][1]);
                                 if (cross[p] & bit) {
@@ -420,7 +404,6 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
                             pq = top ? g[0][1] - g[1][1] : g[1][1] - g[0][1];
                             carry_v = g[1][0];
                             carry_q = g[1][1];
-                            carry = true;
                         }
                         if (pv > vtiny) sink.pair(p, n, m, pair_weight(pv, pq, D2));
                     }
