@@ -42,12 +42,14 @@ constexpr int EV_CAP = 64;         // crossing events queued per warp and round 
 constexpr int KCT_ROWS = 32;       // row boundaries of one voxel (its footprint spans <= 31 rows)
 
 // Brick height along x_3: two runs of SEG voxels per column-cut build (the build is a large
-// part of the per-voxel work), except for the relaxed adjoint (one run: measured faster).
+// part of the per-voxel work). The relaxed adjoint takes one or two runs (RUNS_ = 1 or 2), as
+// the plan chooses from the geometry: two runs share each build along more voxels but overflow
+// the shared tile where a brick's footprint is tall, and its fallback reads y from global memory.
 // Detector tile: 12288 floats for the near-exact kernels (2 blocks per SM), 8192 for the
 // relaxed ones (3 blocks per SM, small static shared memory).
-template <int VARIANT, bool FWD = true>
+template <int VARIANT, bool FWD = true, int RUNS_ = 0>
 struct Brick {
-    static constexpr int RUNS = (VARIANT == 0 || FWD) ? 2 : 1;  // relaxed adjoint: measured faster with 1
+    static constexpr int RUNS = RUNS_ ? RUNS_ : ((VARIANT == 0 || FWD) ? 2 : 1);
     static constexpr int Z = SEG * RUNS;                       // voxels along x_3
     static constexpr int TILE = VARIANT == 0 ? 12288 : 8192;   // floats of the detector tile
     static constexpr int DYN_FLOATS = Z * NCOLS + TILE;        // dynamic shared memory
@@ -736,15 +738,15 @@ __global__ void __launch_bounds__(NTHREADS, VARIANT == 1 ? 3 : 2) fwd_kernel(con
 
 // Adjoint. grid: (bricks in x1 x2, segments along x3, batch); every block loops over all
 // views, staging F y of the brick's footprint in shared memory per view.
-// Dynamic shared memory: Brick<VARIANT>::DYN_FLOATS floats.
-template <int VARIANT, int SCALING>
+// Dynamic shared memory: Brick<VARIANT, false, RUNS_>::DYN_FLOATS floats.
+template <int VARIANT, int SCALING, int RUNS_ = 0>
 __global__ void __launch_bounds__(NTHREADS, VARIANT == 1 ? 3 : 2) bwd_kernel(const View* __restrict__ views, Grid G,
                                                           const float* __restrict__ y, float* __restrict__ vol,
                                                           long long vstride, long long pstride, int accumulate,
                                                           int* err) {
     extern __shared__ float dyn[];
     __shared__ BlockSmem<VARIANT> bs;
-    using B = Brick<VARIANT, false>;
+    using B = Brick<VARIANT, false, RUNS_>;
     float* acc_s = dyn;                 // [NCOLS][B::Z]
     float* tile = dyn + B::Z * NCOLS;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -33,6 +33,7 @@ struct kct_plan {
     int* d_err;
     unsigned long long* d_count;
     int fwd_chunk;                 // views per forward block (kct_plan_autotune may change it)
+    int bwd_runs;                  // relaxed adjoint: runs of 64 voxels per brick (1 or 2)
 };
 
 namespace {
@@ -182,13 +183,55 @@ unsigned bricks(const Grid& G) {
     return (unsigned)(((G.nx + kct::BX - 1) / kct::BX) * ((G.ny + kct::BY - 1) / kct::BY));
 }
 
-template <int VARIANT, bool FWD = true>
+template <int VARIANT, bool FWD = true, int RUNS = 0>
 unsigned segments(const Grid& G) {
-    return (unsigned)((G.nz + kct::Brick<VARIANT, FWD>::Z - 1) / kct::Brick<VARIANT, FWD>::Z);
+    return (unsigned)((G.nz + kct::Brick<VARIANT, FWD, RUNS>::Z - 1) / kct::Brick<VARIANT, FWD, RUNS>::Z);
 }
 
-template <int VARIANT, bool FWD = true>
-constexpr size_t brick_dyn_smem() { return sizeof(float) * kct::Brick<VARIANT, FWD>::DYN_FLOATS; }
+template <int VARIANT, bool FWD = true, int RUNS = 0>
+constexpr size_t brick_dyn_smem() { return sizeof(float) * kct::Brick<VARIANT, FWD, RUNS>::DYN_FLOATS; }
+
+// Fraction of the bricks of bz voxels along x_3 whose detector window (the bounding box of the
+// projected brick corners plus one pixel, clipped to the detector, as the kernels compute it)
+// holds more than `cap` pixels, over up to 8 evenly spaced views and up to 4096 bricks per view.
+double brick_overflow(const double* pmats, int nviews, const kct_volume_desc& vol, const kct_detector_desc& det,
+                      int bz, int cap) {
+    const int nbx = (vol.nx + kct::BX - 1) / kct::BX, nby = (vol.ny + kct::BY - 1) / kct::BY;
+    const int nbz = (vol.nz + bz - 1) / bz;
+    const long long nb = (long long)nbx * nby * nbz;
+    const long long step = nb > 4096 ? nb / 4096 : 1;
+    const int vstep = nviews > 8 ? nviews / 8 : 1;
+    long long over = 0, count = 0;
+    for (int q = 0; q < nviews; q += vstep) {
+        const double* P = pmats + 12 * (size_t)q;
+        for (long long b = 0; b < nb; b += step) {
+            const int bi = (int)(b % nbx), bj = (int)((b / nbx) % nby), bk = (int)(b / ((long long)nbx * nby));
+            const int i0 = bi * kct::BX, j0 = bj * kct::BY, k0 = bk * bz;
+            double umin = 1e300, umax = -1e300, vmin = 1e300, vmax = -1e300;
+            for (int c = 0; c < 8; ++c) {
+                const int ii = (c & 1) ? std::min(i0 + kct::BX, vol.nx) : i0;
+                const int jj = (c & 2) ? std::min(j0 + kct::BY, vol.ny) : j0;
+                const int kk = (c & 4) ? std::min(k0 + bz, vol.nz) : k0;
+                const double X = (ii - 0.5 * vol.nx) * vol.ax, Y = (jj - 0.5 * vol.ny) * vol.ay, Z = (kk - 0.5 * vol.nz) * vol.az;
+                const double w = P[8] * X + P[9] * Y + P[10] * Z + P[11];
+                const double u = (P[0] * X + P[1] * Y + P[2] * Z + P[3]) / w;
+                const double v = (P[4] * X + P[5] * Y + P[6] * Z + P[7]) / w;
+                umin = std::fmin(umin, u);
+                umax = std::fmax(umax, u);
+                vmin = std::fmin(vmin, v);
+                vmax = std::fmax(vmax, v);
+            }
+            const long long u0 = std::max((long long)std::floor(umin + 0.5) - 1, 0LL);
+            const long long u1 = std::min((long long)std::floor(umax + 0.5) + 1, (long long)det.nu - 1);
+            const long long v0 = std::max((long long)std::floor(vmin + 0.5) - 1, 0LL);
+            const long long v1 = std::min((long long)std::floor(vmax + 0.5) + 1, (long long)det.nv - 1);
+            const long long area = (u1 >= u0 && v1 >= v0) ? (u1 - u0 + 1) * (v1 - v0 + 1) : 0;
+            over += area > cap ? 1 : 0;
+            ++count;
+        }
+    }
+    return count ? (double)over / count : 0.0;
+}
 
 // opt in to more than 48 KB of shared memory per block (once per process)
 template <class K>
@@ -209,6 +252,8 @@ cudaError_t brick_kernel_attributes() {
         e = set_dyn(kct::bwd_kernel<0, 1>, brick_dyn_smem<0, false>(), e);
         e = set_dyn(kct::bwd_kernel<1, 0>, brick_dyn_smem<1, false>(), e);
         e = set_dyn(kct::bwd_kernel<1, 1>, brick_dyn_smem<1, false>(), e);
+        e = set_dyn(kct::bwd_kernel<1, 0, 2>, brick_dyn_smem<1, false, 2>(), e);
+        e = set_dyn(kct::bwd_kernel<1, 1, 2>, brick_dyn_smem<1, false, 2>(), e);
         return e;
     }();
     return done;
@@ -242,13 +287,19 @@ void launch_fwd_any(const kct_plan* p, const Grid& G, int chunk, const float* vo
     }
 }
 
+template <int VARIANT, int SCALING, int RUNS = 0>
+void launch_bwd_runs(const kct_plan* p, const float* y, float* vol, int nbatch, int accumulate, cudaStream_t st) {
+    const Grid& G = p->grid;
+    dim3 grid(bricks(G), segments<VARIANT, false, RUNS>(G), (unsigned)nbatch);
+    const long long vs = (long long)G.nx * G.ny * G.nz, ps = (long long)G.nu * G.nv * G.nviews;
+    kct::bwd_kernel<VARIANT, SCALING, RUNS><<<grid, kct::NTHREADS, brick_dyn_smem<VARIANT, false, RUNS>(), st>>>(
+        p->d_views, G, y, vol, vs, ps, accumulate, p->d_err);
+}
+
 template <int VARIANT, int SCALING>
 void launch_bwd(const kct_plan* p, const float* y, float* vol, int nbatch, int accumulate, cudaStream_t st) {
-    const Grid& G = p->grid;
-    dim3 grid(bricks(G), segments<VARIANT, false>(G), (unsigned)nbatch);
-    const long long vs = (long long)G.nx * G.ny * G.nz, ps = (long long)G.nu * G.nv * G.nviews;
-    kct::bwd_kernel<VARIANT, SCALING><<<grid, kct::NTHREADS, brick_dyn_smem<VARIANT, false>(), st>>>(p->d_views, G, y, vol, vs, ps,
-                                                                                   accumulate, p->d_err);
+    if (VARIANT == 1 && p->bwd_runs == 2) launch_bwd_runs<VARIANT, SCALING, 2>(p, y, vol, nbatch, accumulate, st);
+    else launch_bwd_runs<VARIANT, SCALING>(p, y, vol, nbatch, accumulate, st);
 }
 
 template <int VARIANT>
@@ -326,6 +377,10 @@ kct_status kct_plan_create(kct_plan** out, const kct_volume_desc* vol, const kct
     p->d_err = nullptr;
     p->d_count = nullptr;
     p->fwd_chunk = kct::VIEW_CHUNK;
+    // relaxed adjoint: two runs per brick where (almost) every brick's footprint fits the tile
+    p->bwd_runs = (variant == KCT_CVP_RELAXED &&
+                   brick_overflow(pmats, nviews, *vol, *det, kct::Brick<1, false, 2>::Z, kct::Brick<1, false, 2>::TILE) <= 0.02)
+                      ? 2 : 1;
     p->h_views.resize(nviews);
     for (int q = 0; q < nviews; ++q) {
         std::string why = setup_view(pmats + 12 * q, *vol, p->h_views[q]);
