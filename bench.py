@@ -41,14 +41,14 @@ UNIT = "Gvoxel·views/s"
 # per view, the adjoint reads one projection tile per view and writes the volume once, so
 # traffic is scaled as below.
 NCU = {
-    "exact project": {"flop_per_vv": 868.4, "warp_per_vv": 103.6, "simt": 0.60,
-                      "dram_read_8": 5.77e8, "dram_write_8": 3.06e7},
-    "exact backproject": {"flop_per_vv": 937.8, "warp_per_vv": 108.9, "simt": 0.62,
-                          "dram_read_8": 5.72e7, "dram_write_8": 4.94e8},
+    "exact project": {"flop_per_vv": 887.3, "warp_per_vv": 94.8, "simt": 0.67,
+                      "dram_read_8": 5.77e8, "dram_write_8": 3.13e7},
+    "exact backproject": {"flop_per_vv": 957.2, "warp_per_vv": 99.6, "simt": 0.69,
+                          "dram_read_8": 5.92e7, "dram_write_8": 4.93e8},
     "relaxed project": {"flop_per_vv": 187.0, "warp_per_vv": 26.6, "simt": 0.66,
-                        "dram_read_8": 5.76e8, "dram_write_8": 3.26e7},
+                        "dram_read_8": 5.79e8, "dram_write_8": 3.29e7},
     "relaxed backproject": {"flop_per_vv": 232.1, "warp_per_vv": 36.3, "simt": 0.61,
-                            "dram_read_8": 5.28e7, "dram_write_8": 4.97e8},
+                            "dram_read_8": 5.34e7, "dram_write_8": 4.98e8},
 }
 
 
@@ -258,7 +258,8 @@ CGLS_DESC = ("cgls128: 128^3 voxels @ 0.5 mm, 180 views / 360 deg, SID 750 / SDD
 def run_cgls(dev, scaling: str, max_iter: int, tol: float = 1e-3):
     """Time to the normal-equation residual |A^T(b - A x)| / |A^T b| <= tol with kct_cgls, for
     both variants, on noisy projections of a seeded phantom made with the same variant.
-    The timed region is the whole kct_cgls call (start, steps, per-step residual reads)."""
+    The timed region is the whole kct_cgls call (start, steps, per-step residual reads); for the
+    relaxed variant also from the learned warm start (run_warm_start)."""
     import torch
 
     from paper_2110_09841_b300 import inputs
@@ -285,7 +286,47 @@ def run_cgls(dev, scaling: str, max_iter: int, tol: float = 1e-3):
                   "ms_per_iteration": ms / max(k, 1), "normal_residual": float(info["normal"][-1]),
                   "data_residual": float(info["data"][-1]),
                   "rel_error_vs_phantom": float((x - truth).norm() / truth.norm())}
+        if v == "relaxed":
+            out["relaxed_warm_start"] = run_warm_start(A, b, truth, ws, max_iter, tol)
     return out
+
+
+def run_warm_start(A, b, truth, ws, max_iter: int, tol: float):
+    """CGLS from the learned warm start (the stored U-Net, trained for this geometry with the
+    relaxed operator): the timed region is the backprojection of b (the network input, reused by
+    CGLS as A^T b), the network's inference and CGLS from its output to the same residual."""
+    import torch
+
+    from paper_2110_09841_b300 import warmstart
+    from paper_2110_09841_b300.unet import UNet3D
+
+    path = os.path.join(ROOT, "paper_2110_09841_b300", "weights", "unet_cgls128.pt")
+    if not os.path.exists(path):
+        return None
+    model = warmstart.load_model(UNet3D().cuda(), path)
+    ones = torch.ones(A.geom.vol_shape, device="cuda")
+    norm = A.backproject(A.project(ones))
+    norm.clamp_(min=1e-6 * float(norm.max()))
+    x = torch.empty(A.geom.vol_shape, dtype=torch.float32, device="cuda")
+
+    def solve():
+        atb = A.backproject(b)
+        with torch.no_grad():
+            x0 = model((atb / norm)[None])[0].contiguous()
+        return A.cgls(b, x0=x0, max_iter=max_iter, tol=tol, out=x, workspace=ws, atb=atb)
+
+    solve()                                                      # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    x, info = solve()
+    e1.record()
+    torch.cuda.synchronize()
+    k = info["iterations"]
+    return {"iterations": k, "converged": info["converged"], "time_s": e0.elapsed_time(e1) / 1e3,
+            "start_normal_residual": float(info["normal"][0]), "normal_residual": float(info["normal"][-1]),
+            "rel_error_vs_phantom": float((x - truth).norm() / truth.norm()),
+            "network": "3D U-Net 16/32/64/128, BF16 tcgen05 convolutions, weights/unet_cgls128.pt"}
 
 
 def bench_config(args, world: int) -> dict:
