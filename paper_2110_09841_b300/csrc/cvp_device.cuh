@@ -24,8 +24,9 @@
 // When both planes stay inside the voxel over the base the integrand is linear in t' and
 // the pair is a closed form of the moments of H_n (weights 1, t', t'^2, lambda, lambda t',
 // lambda = t_c t' + xi_c xi'). A plane that leaves the voxel through a face needs the
-// moments of H_n ∩ {t' < tau}; all polygon moments are exact Green's-theorem sums over
-// the boundary of the convex polygon base ∩ half-planes.
+// moments of H_n ∩ {t' < tau}: the chord of H_n at depth t' is linear in t' between vertex
+// depths, so each moment is a cubic in tau there, evaluated exactly from a per-column
+// depth profile of H_n (depth_profile, profile_cut).
 // The weight is W = V / |c - s|^2 with c the centre of mass of the cut:
 //     |c - s|^2 = |D + M/V|^2 ~ (V |D|^2 + 2 D.M) / V       (D = x_vox - s),
 // the dropped |M/V|^2 / |D|^2 <= 3/4 (a / r)^2 being below the FP32 resolution of r^2 for
@@ -55,8 +56,6 @@ struct View {
     float sgv;                   // sign(gv)
     float fcos;                  // |gu gv| = f^2 / (pixel area)
     float sq_t[4], sq_x[4];      // voxel base square vertices (t', xi'), counter-clockwise
-    float tmin_sq, tmax_sq;      // t' range of the square
-    float sq_tt, sq_tx;          // Green sums of the full square for t'^2 and t' xi'
     float sx, sy;                // source s_1, s_2 (used by the ray-driven comparator only)
     float cv_lo, inv_agv_lo;     // low-order parts of cv and 1/|gv|
     float sz_lo;                 // low-order part of s_3
@@ -116,47 +115,40 @@ KCT_HD float pixel_factor(const View& V, int n, int m) {
 }
 
 // ----------------------------------------------------------------------------------------
-// Green's theorem sums over directed segments in the (t', xi') plane
+// Green's theorem over the directed edges of a polygon in the (t', xi') plane
 // ----------------------------------------------------------------------------------------
 
-struct Mom5 {
-    float a, t, x, tt, tx;   // sums of c, c(t0+t1), c(x0+x1), c(t0^2+t0 t1+t1^2), c(2t0x0+t0x1+t1x0+2t1x1)
+struct Green2 {
+    float a, t;   // sums of c and c (t0 + t1), c = t0 x1 - t1 x0: twice the area, six times the t' moment
 };
 
-KCT_HD Mom5 mom_zero() { return Mom5{0.f, 0.f, 0.f, 0.f, 0.f}; }
-
-template <bool FULL>
-KCT_HD void seg_acc(Mom5& m, float pt, float px, float qt, float qx) {
-    float c = pt * qx - qt * px;
+KCT_HD void seg_acc(Green2& m, float pt, float px, float qt, float qx) {
+    const float c = pt * qx - qt * px;
     m.a += c;
     m.t = fmaf(c, pt + qt, m.t);
-    if (FULL) {
-        m.x = fmaf(c, px + qx, m.x);
-        m.tt = fmaf(c, fmaf(pt, pt, fmaf(pt, qt, qt * qt)), m.tt);
-        m.tx = fmaf(c, fmaf(2.f * pt, px, fmaf(pt, qx, fmaf(qt, px, 2.f * qt * qx))), m.tx);
-    }
 }
+
+// 1/x to about 2 ulp (the hardware reciprocal on the device) for 2^-126 < |x| < 2^126
+KCT_HD float rcp_fast(float x) {
+#ifdef __CUDA_ARCH__
+    return __fdividef(1.f, x);
+#else
+    return 1.f / x;
+#endif
+}
+
+// p / (p - q) for p, q of opposite signs (where a segment crosses a line), in [0, 1]
+KCT_HD float cross_frac(float p, float q) { return fminf(fmaxf(p * rcp_fast(p - q), 0.f), 1.f); }
 
 // restrict the parameter interval [s0, s1] of a segment to {L < 0}; L linear along it
 KCT_HD void clip_param(float Lp, float Lq, float& s0, float& s1) {
     bool pin = Lp < 0.f, qin = Lq < 0.f;
     if (pin != qin) {
-        float ss = Lp / (Lp - Lq);
+        float ss = cross_frac(Lp, Lq);
         if (pin) s1 = fminf(s1, ss);
         else s0 = fmaxf(s0, ss);
     } else if (!pin) {
         s1 = -1.f;
-    }
-}
-
-// accumulate the part [s0, s1] of segment p -> q
-template <bool FULL>
-KCT_HD void seg_part(Mom5& m, float pt, float px, float qt, float qx, float s0, float s1) {
-    if (s1 > s0) {
-        float dt = qt - pt, dx = qx - px;
-        float at = fmaf(s0, dt, pt), ax = fmaf(s0, dx, px);
-        float bt = fmaf(-(1.f - s1), dt, qt), bx = fmaf(-(1.f - s1), dx, qx);
-        seg_acc<FULL>(m, at, ax, bt, bx);
     }
 }
 
@@ -188,11 +180,11 @@ KCT_HD int clip_square(const View& V, const Line& l0, const Line& l1, float* pt,
         float s[2];
         int ns = 0;
         if ((A0 < 0.f) != (B0 < 0.f)) {
-            const float ss = A0 / (A0 - B0);
+            const float ss = cross_frac(A0, B0);
             if (ss >= a1 && ss <= b1) s[ns++] = ss;
         }
         if ((A1 < 0.f) != (B1 < 0.f)) {
-            const float ss = A1 / (A1 - B1);
+            const float ss = cross_frac(A1, B1);
             if (ss >= a0 && ss <= b0) s[ns++] = ss;
         }
         if (ns == 2 && s[1] < s[0]) { const float q = s[0]; s[0] = s[1]; s[1] = q; }
@@ -203,6 +195,115 @@ KCT_HD int clip_square(const View& V, const Line& l0, const Line& l1, float* pt,
         }
     }
     return nv;
+}
+
+// ----------------------------------------------------------------------------------------
+// Depth profile of a convex polygon: the moments of its part below a depth t' = tau
+// ----------------------------------------------------------------------------------------
+
+constexpr int KCT_IV = 7;        // depth intervals of H_n (its at most 8 vertices give at most 7)
+
+// Between two consecutive vertex depths T_j < T_(j+1) the chord of a convex polygon at depth
+// t' joins the same two edges, so its length w and midpoint c are linear in t'. The moments
+// (1, t', t'^2, xi', t' xi') of the part below tau then grow by the integrals of w, w t',
+// w t'^2, w c and w c t' from T_j to tau: polynomials of degree <= 3 in t', which Simpson's
+// rule integrates exactly. simpson5 adds them for [t0, t1], s = t1 - t0, with the chord at t0
+// (w0, c0) and its change over the interval (dw, dc) taken at the fraction lam of it.
+KCT_HD void simpson5(float t0, float t1, float s, float lam, float w0, float dw, float c0, float dc, float& A,
+                     float& T, float& TT, float& X, float& TX) {
+    const float hl = 0.5f * lam;
+    const float wm4 = 4.f * fmaf(hl, dw, w0), w1 = fmaf(lam, dw, w0);
+    const float cm = fmaf(hl, dc, c0), c1 = fmaf(lam, dc, c0);
+    const float tm = fmaf(0.5f, s, t0);
+    const float a0t = w0 * t0, amt = wm4 * tm, a1t = w1 * t1;
+    const float a0c = w0 * c0, amc = wm4 * cm, a1c = w1 * c1;
+    const float h6 = s * (1.f / 6.f);
+    A = fmaf(h6, w0 + wm4 + w1, A);
+    T = fmaf(h6, a0t + amt + a1t, T);
+    TT = fmaf(h6, fmaf(a0t, t0, fmaf(amt, tm, a1t * t1)), TT);
+    X = fmaf(h6, a0c + amc + a1c, X);
+    TX = fmaf(h6, fmaf(a0c, t0, fmaf(amc, tm, a1c * t1)), TX);
+}
+
+// The profile of the convex polygon (pt, px)[0 .. nv) (vertices in order, either sense):
+// the interval starts st[j] = T_j (st[K .. 7] = +inf) and per depth interval j,
+// a[j] = (1 / (T_(j+1) - T_j), w(T_j), w(T_(j+1)) - w(T_j), c(T_j)),
+// b[j] = (c(T_(j+1)) - c(T_j), the area, t' and t'^2 moments of the part below T_j) and
+// m[j] = its xi' and t' xi' moments. The two chains from the lowest to the highest vertex
+// are walked together; w and c at an interval's ends come from the two edges that span it.
+// Returns the number of intervals (0 for a degenerate polygon); the moments of the whole
+// polygon go to full and its depth range to tlo, thi.
+KCT_HD int depth_profile(const float* pt, const float* px, int nv, float* st, float4* a, float4* b, float2* m,
+                         float (&full)[5], float& tlo, float& thi) {
+    float A = 0.f, T = 0.f, TT = 0.f, X = 0.f, TX = 0.f;
+    int imin = 0, imax = 0;
+    for (int e = 1; e < nv; ++e) {
+        if (pt[e] < pt[imin]) imin = e;
+        if (pt[e] > pt[imax]) imax = e;
+    }
+    tlo = nv > 0 ? pt[imin] : 0.f;
+    thi = nv > 0 ? pt[imax] : 0.f;
+    int K = 0;
+    if (nv >= 3) {
+        int ia = imin, ib = imin;      // the chains forward and backward from the lowest vertex
+        float Tc = tlo;
+        for (int it = 0; it < KCT_IV && Tc < thi; ++it) {
+            // pass the vertices at depth <= Tc (neither chain can pass the highest vertex)
+            for (int q = 0; q < nv; ++q) {
+                const int na = ia + 1 == nv ? 0 : ia + 1;
+                if (pt[na] > Tc) break;
+                ia = na;
+            }
+            for (int q = 0; q < nv; ++q) {
+                const int nb = ib == 0 ? nv - 1 : ib - 1;
+                if (pt[nb] > Tc) break;
+                ib = nb;
+            }
+            const int na = ia + 1 == nv ? 0 : ia + 1, nb = ib == 0 ? nv - 1 : ib - 1;
+            const float Tn = fminf(fminf(pt[na], pt[nb]), thi);
+            // both edges span [Tc, Tn]: pt[ia], pt[ib] <= Tc < Tn <= pt[na], pt[nb]
+            const float ra = rcp_fast(pt[na] - pt[ia]), rb = rcp_fast(pt[nb] - pt[ib]);
+            const float dxa = px[na] - px[ia], dxb = px[nb] - px[ib];
+            const float xa0 = fmaf((Tc - pt[ia]) * ra, dxa, px[ia]), xa1 = fmaf((Tn - pt[ia]) * ra, dxa, px[ia]);
+            const float xb0 = fmaf((Tc - pt[ib]) * rb, dxb, px[ib]), xb1 = fmaf((Tn - pt[ib]) * rb, dxb, px[ib]);
+            const float w0 = fabsf(xb0 - xa0), w1 = fabsf(xb1 - xa1);
+            const float c0 = 0.5f * (xa0 + xb0), c1 = 0.5f * (xa1 + xb1);
+            st[K] = Tc;
+            a[K] = make_float4(rcp_fast(Tn - Tc), w0, w1 - w0, c0);
+            b[K] = make_float4(c1 - c0, A, T, TT);
+            m[K] = make_float2(X, TX);
+            simpson5(Tc, Tn, Tn - Tc, 1.f, w0, w1 - w0, c0, c1 - c0, A, T, TT, X, TX);
+            ++K;
+            Tc = Tn;
+        }
+    }
+    for (int j = K; j < KCT_IV + 1; ++j) st[j] = 3.0e38f;
+    full[0] = A;
+    full[1] = T;
+    full[2] = TT;
+    full[3] = X;
+    full[4] = TX;
+    return K;
+}
+
+// Moments (1, t', t'^2, xi', t' xi') of the part below tau of a polygon with profile
+// (st, a, b, m), for T_0 <= tau <= T_K: the interval holding tau is the number of interval
+// starts T_1 .. T_7 at or below it (two vector loads, the same for every thread of a column).
+KCT_HD void profile_cut(const float* st, const float4* a, const float4* b, const float2* m, float tau, float& A,
+                        float& T, float& TT, float& X, float& TX) {
+    const float4 s0 = reinterpret_cast<const float4*>(st)[0], s1 = reinterpret_cast<const float4*>(st)[1];
+    const int j = (tau >= s0.y) + (tau >= s0.z) + (tau >= s0.w) + (tau >= s1.x) + (tau >= s1.y) + (tau >= s1.z) +
+                  (tau >= s1.w);
+    const float4 aj = a[j], bj = b[j];
+    const float2 mj = m[j];
+    const float t0 = st[j];
+    A = bj.y;
+    T = bj.z;
+    TT = bj.w;
+    X = mj.x;
+    TX = mj.y;
+    const float s = tau - t0;
+    simpson5(t0, tau, s, s * aj.x, aj.y, aj.z, aj.w, bj.x, A, T, TT, X, TX);
 }
 
 // ----------------------------------------------------------------------------------------
@@ -286,22 +387,10 @@ KCT_HD bool column_setup(const View& V, const Grid& G, int i, int j, Column& C) 
 // Column cuts and their moments
 // ----------------------------------------------------------------------------------------
 
-// normalised moments of a Green-sum record: 1, t', t'^2, lambda, lambda t'
+// moments of a part of H_n: 1, t', t'^2, lambda, lambda t'
 struct Mom {
     float m1, mt, mtt, ml, mlt;
 };
-
-KCT_HD Mom normalise(const Mom5& g, float tc, float xc) {
-    Mom r;
-    r.m1 = 0.5f * g.a;
-    r.mt = g.t * (1.f / 6.f);
-    float mx = g.x * (1.f / 6.f);
-    r.mtt = g.tt * (1.f / 12.f);
-    float mtx = g.tx * (1.f / 24.f);
-    r.ml = fmaf(tc, r.mt, xc * mx);
-    r.mlt = fmaf(tc, r.mtt, xc * mtx);
-    return r;
-}
 
 KCT_HD Mom mom_sub(const Mom& a, const Mom& b) {
     return Mom{a.m1 - b.m1, a.mt - b.mt, a.mtt - b.mtt, a.ml - b.ml, a.mlt - b.mlt};

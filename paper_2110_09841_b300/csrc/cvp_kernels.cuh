@@ -61,12 +61,13 @@ constexpr unsigned FULLMASK = 0xffffffffu;
 
 struct WarpSmem {
     Column C;                      // the warp's current column
-    float pt[KCT_CB][8], px[KCT_CB][8];   // vertices of H_n, n = cstart + c
-    int nv[KCT_CB];
+    alignas(16) float ivs[KCT_CB][KCT_IV + 1];   // exact: depth profile of H_n, n = cstart + c (depth_profile)
+    float4 iva[KCT_CB][KCT_IV];
+    float4 ivb[KCT_CB][KCT_IV];
+    float2 ivm[KCT_CB][KCT_IV];
     float4 fa[KCT_CB];             // exact: moments of H_n m1, mt, mtt, ml; relaxed: A_n, t_n, 1/t_n, -
     float4 fb[KCT_CB];             // exact: mlt, t'-range of H_n (lo, hi), -
     float2 fr[KCT_CB];             // exact: 1 / depth at the two ends of that range
-    float eg[KCT_CB][8][5];        // exact: Green terms of each whole edge of H_n (a, t, x, tt, tx)
     float ev_p0[EV_CAP], ev_p1[EV_CAP], ev_zs[EV_CAP];
     float res_v[EV_CAP], res_q[EV_CAP];
 };
@@ -75,6 +76,7 @@ struct WarpSmem {
 // blocks stay small.
 struct WarpSmemRelaxed {
     Column C;
+    float pt[KCT_CB][8], px[KCT_CB][8];   // vertices of H_n (build scratch)
     float4 fa[KCT_CB];             // A_n t_n / |gv|, t'_CM / t_n, 1/t_n, half the voxel's projected row extent
 };
 
@@ -92,39 +94,17 @@ struct BlockSmemOf {
 template <int VARIANT>
 using BlockSmem = BlockSmemOf<typename std::conditional<VARIANT == 0, WarpSmem, WarpSmemRelaxed>::type>;
 
-// Moments (1, t', t'^2, lambda, lambda t') of H_n ∩ {t' < tau} from the vertices of H_n:
-// Green's theorem over the boundary of the cut, i.e. the edges below tau (their whole-edge
-// terms are precomputed in eg), the clipped parts of the two edges that cross t' = tau, and
-// the chord along t' = tau.
-// Not inlined: the clipping exists once in the code and its callers stay small.
-__device__ __noinline__ Mom cut_moments_call(const float* pt, const float* px, const float (*eg)[5], int nv,
-                                             float tau, float tc, float xc) {
-    Mom5 m = mom_zero();
-    float xt = 0.f, xx = 0.f, nt = 0.f, nx = 0.f;
-    bool hx = false, hn = false;
-    for (int e = 0; e < nv; ++e) {
-        const int f = (e + 1 == nv) ? 0 : e + 1;
-        const float at = pt[e], bt = pt[f];
-        const float La = at - tau, Lb = bt - tau;
-        if (La < 0.f && Lb < 0.f) {
-            m.a += eg[e][0];
-            m.t += eg[e][1];
-            m.x += eg[e][2];
-            m.tt += eg[e][3];
-            m.tx += eg[e][4];
-        } else if ((La < 0.f) != (Lb < 0.f)) {
-            const float ax = px[e], bx = px[f];
-            float s0 = 0.f, s1 = 1.f;
-            clip_param(La, Lb, s0, s1);
-            seg_part<true>(m, at, ax, bt, bx, s0, s1);
-            const float ss = La / (La - Lb);
-            const float ct = fmaf(ss, bt - at, at), cx = fmaf(ss, bx - ax, ax);
-            if (La < 0.f) { xt = ct; xx = cx; hx = true; }
-            else { nt = ct; nx = cx; hn = true; }
-        }
-    }
-    if (hx && hn) seg_acc<true>(m, xt, xx, nt, nx);
-    return normalise(m, tc, xc);
+// Moments (1, t', t'^2, lambda, lambda t') of H_n ∩ {t' < tau}, tlo <= tau <= thi, from the
+// depth profile of H_n in slot c: one interval's closed form, the same work for every tau.
+__device__ __forceinline__ Mom cut_moments(const WarpSmem* ws, int c, float tau, float tc, float xc) {
+    float A, T, TT, X, TX;
+    profile_cut(ws->ivs[c], ws->iva[c], ws->ivb[c], ws->ivm[c], tau, A, T, TT, X, TX);
+    return Mom{A, T, TT, fmaf(tc, T, xc * X), fmaf(tc, TT, xc * TX)};
+}
+
+// the same, not inlined, for the rare second cut of a plane that crosses both faces
+__device__ __noinline__ Mom cut_moments_call(const WarpSmem* ws, int c, float tau, float tc, float xc) {
+    return cut_moments(ws, c, tau, tc, xc);
 }
 
 // Volume and first moment along D of {(t', xi') in H_n, 0 < height < clamp(p0 + p1 t', 0, az)}
@@ -344,8 +324,8 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
                     // second one only for planes that cross both faces within H_n).
                     const bool in0 = tau0 > tlo && tau0 < thi, in1 = tau1 > tlo && tau1 < thi;
                     Mom ca = zero_m, cb = zero_m;
-                    if (in0 || in1) ca = cut_moments_call(ws->pt[c], ws->px[c], ws->eg[c], ws->nv[c], in0 ? tau0 : tau1, C.tc, C.xc);
-                    if (in0 && in1) cb = cut_moments_call(ws->pt[c], ws->px[c], ws->eg[c], ws->nv[c], tau1, C.tc, C.xc);
+                    if (in0 || in1) ca = cut_moments(ws, c, in0 ? tau0 : tau1, C.tc, C.xc);
+                    if (in0 && in1) cb = cut_moments_call(ws, c, tau1, C.tc, C.xc);
                     const Mom c0 = in0 ? ca : (tau0 <= tlo) ? zero_m : full_m;
                     const Mom c1 = in1 ? (in0 ? cb : ca) : (tau1 <= tlo) ? zero_m : full_m;
                     float gv, gq;
@@ -475,54 +455,35 @@ __device__ __noinline__ void build_column_cut(const View* Vp, const Column* Cp, 
     const Column& C = *Cp;
     Line lo, hi;
     column_lines(V, C, n, lo, hi);
-    float pt[8], px[8];
+    float* pt = ws->pt[c];
+    float* px = ws->px[c];
     const int nv = clip_square(V, lo, hi, pt, px);
-    Mom5 g = mom_zero();
+    Green2 g{0.f, 0.f};
     for (int e = 0; e < nv; ++e) {
         const int f = (e + 1 == nv) ? 0 : e + 1;
-        seg_acc<false>(g, pt[e], px[e], pt[f], px[f]);
+        seg_acc(g, pt[e], px[e], pt[f], px[f]);
     }
     const float m1 = 0.5f * g.a, mt = g.t * (1.f / 6.f);
-    const float tcm = m1 > 0.f ? mt / m1 : 0.f;            // t' of the centre of mass of H_n
-    const float tn = C.tc + tcm, itn = 1.0f / tn;
+    const float tcm = m1 > 0.f ? mt * rcp_fast(m1) : 0.f;  // t' of the centre of mass of H_n
+    const float tn = C.tc + tcm, itn = rcp_fast(tn);
     ws->fa[c] = make_float4(m1 * tn * V.inv_agv, tcm * itn, itn, 0.5f * az * fabsf(V.gv) * itn);
 }
 
-// H_n for detector column n, near-exact variant: its vertices, the Green terms of its edges,
-// its moments and depth range into slot c. Not inlined: it runs once per column and view.
+// H_n for detector column n, near-exact variant: its depth profile, moments and depth range
+// into slot c. Not inlined: it runs once per column and view.
 __device__ __noinline__ void build_column_cut(const View* Vp, const Column* Cp, float az, int n, WarpSmem* ws,
                                               int c) {
     const View& V = *Vp;
     const Column& C = *Cp;
     Line lo, hi;
     column_lines(V, C, n, lo, hi);
-    float* pt = ws->pt[c];
-    float* px = ws->px[c];
+    float* pt = ws->ev_p0 + 8 * c;     // scratch: the event queue is idle while cuts are built
+    float* px = ws->ev_p1 + 8 * c;
     const int nv = clip_square(V, lo, hi, pt, px);
-    ws->nv[c] = nv;
-    // Green terms of each edge (kept for the cuts at crossing depths) and their sum
-    Mom5 g = mom_zero();
-    float tlo = 3.0e38f, thi = -3.0e38f;
-    for (int e = 0; e < nv; ++e) {
-        const int f = (e + 1 == nv) ? 0 : e + 1;
-        Mom5 m = mom_zero();
-        seg_acc<true>(m, pt[e], px[e], pt[f], px[f]);
-        ws->eg[c][e][0] = m.a;
-        ws->eg[c][e][1] = m.t;
-        ws->eg[c][e][2] = m.x;
-        ws->eg[c][e][3] = m.tt;
-        ws->eg[c][e][4] = m.tx;
-        g.a += m.a;
-        g.t += m.t;
-        g.x += m.x;
-        g.tt += m.tt;
-        g.tx += m.tx;
-        tlo = fminf(tlo, pt[e]);
-        thi = fmaxf(thi, pt[e]);
-    }
-    const Mom f = normalise(g, C.tc, C.xc);
-    ws->fa[c] = make_float4(f.m1, f.mt, f.mtt, f.ml);
-    ws->fb[c] = make_float4(f.mlt, tlo, thi, 0.f);
+    float g[5], tlo, thi;
+    depth_profile(pt, px, nv, ws->ivs[c], ws->iva[c], ws->ivb[c], ws->ivm[c], g, tlo, thi);
+    ws->fa[c] = make_float4(g[0], g[1], g[2], fmaf(C.tc, g[1], C.xc * g[3]));
+    ws->fb[c] = make_float4(fmaf(C.tc, g[2], C.xc * g[4]), tlo, thi, 0.f);
     ws->fr[c] = make_float2(1.0f / (C.tc + tlo), 1.0f / (C.tc + thi));
 }
 

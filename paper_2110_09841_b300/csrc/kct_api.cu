@@ -142,26 +142,12 @@ std::string setup_view(const double* P, const kct_volume_desc& vol, View& V) {
     const double qx[4] = {-0.5 * vol.ax, 0.5 * vol.ax, 0.5 * vol.ax, -0.5 * vol.ax};
     const double qy[4] = {-0.5 * vol.ay, -0.5 * vol.ay, 0.5 * vol.ay, 0.5 * vol.ay};
     double tt[4], xx[4];
-    double tmn = 1e300, tmx = -1e300;
     for (int e = 0; e < 4; ++e) {
         tt[e] = wx * qx[e] + wy * qy[e];
         xx[e] = hx * qx[e] + hy * qy[e];
         V.sq_t[e] = (float)tt[e];
         V.sq_x[e] = (float)xx[e];
-        tmn = std::fmin(tmn, tt[e]);
-        tmx = std::fmax(tmx, tt[e]);
     }
-    V.tmin_sq = (float)tmn;
-    V.tmax_sq = (float)tmx;
-    double stt = 0.0, stx = 0.0;
-    for (int e = 0; e < 4; ++e) {
-        int f = (e + 1) & 3;
-        double c = tt[e] * xx[f] - tt[f] * xx[e];
-        stt += c * (tt[e] * tt[e] + tt[e] * tt[f] + tt[f] * tt[f]);
-        stx += c * (2 * tt[e] * xx[e] + tt[e] * xx[f] + tt[f] * xx[e] + 2 * tt[f] * xx[f]);
-    }
-    V.sq_tt = (float)stt;
-    V.sq_tx = (float)stx;
     V.sx = (float)s[0];
     V.sy = (float)s[1];
     V.cv_lo = (float)(cv - (double)V.cv);
