@@ -162,36 +162,47 @@ KCT_HD Line line_none() { return Line{0.f, 0.f, 1.f}; }
 
 KCT_HD float line_eval(const Line& l, float t, float x) { return fmaf(l.at, t, fmaf(l.ax, x, -l.c)); }
 
-// Vertices (counter-clockwise) of the square clipped by two half-planes: each square edge
-// contributes its start vertex when inside both, then, in order along the edge, the points
-// where it crosses a line while inside the other half-plane. At most 8 points.
+// The points that square edge e contributes to the square clipped by two half-planes: its
+// start vertex when inside both, then, in order along the edge, the points where it crosses
+// a line while inside the other half-plane (ot, ox)[0 .. n), n <= 3.
+KCT_HD int clip_square_edge(const View& V, const Line& l0, const Line& l1, int e, float (&ot)[3], float (&ox)[3]) {
+    const int f = (e + 1) & 3;
+    const float at = V.sq_t[e], ax = V.sq_x[e], bt = V.sq_t[f], bx = V.sq_x[f];
+    const float A0 = line_eval(l0, at, ax), B0 = line_eval(l0, bt, bx);
+    const float A1 = line_eval(l1, at, ax), B1 = line_eval(l1, bt, bx);
+    const bool sv = A0 < 0.f && A1 < 0.f;
+    // inside parameter intervals of the edge for each line
+    float a0 = 0.f, b0 = 1.f, a1 = 0.f, b1 = 1.f;
+    clip_param(A0, B0, a0, b0);
+    clip_param(A1, B1, a1, b1);
+    const float s0 = cross_frac(A0, B0), s1 = cross_frac(A1, B1);
+    const bool h0 = ((A0 < 0.f) != (B0 < 0.f)) && s0 >= a1 && s0 <= b1;
+    const bool h1 = ((A1 < 0.f) != (B1 < 0.f)) && s1 >= a0 && s1 <= b0;
+    const float sa = h0 ? (h1 ? fminf(s0, s1) : s0) : s1, sb = fmaxf(s0, s1);
+    const float cat = fmaf(sa, bt - at, at), cax = fmaf(sa, bx - ax, ax);
+    const float cbt = fmaf(sb, bt - at, at), cbx = fmaf(sb, bx - ax, ax);
+    ot[0] = sv ? at : cat;
+    ox[0] = sv ? ax : cax;
+    ot[1] = sv ? cat : cbt;
+    ox[1] = sv ? cax : cbx;
+    ot[2] = cbt;
+    ox[2] = cbx;
+    return (int)sv + (int)h0 + (int)h1;
+}
+
+// Vertices (counter-clockwise) of the square clipped by two half-planes, edge by edge
+// (clip_square_edge); at most 8 are kept.
 KCT_HD int clip_square(const View& V, const Line& l0, const Line& l1, float* pt, float* px) {
     int nv = 0;
     for (int e = 0; e < 4; ++e) {
-        const int f = (e + 1) & 3;
-        const float at = V.sq_t[e], ax = V.sq_x[e], bt = V.sq_t[f], bx = V.sq_x[f];
-        const float A0 = line_eval(l0, at, ax), B0 = line_eval(l0, bt, bx);
-        const float A1 = line_eval(l1, at, ax), B1 = line_eval(l1, bt, bx);
-        if (A0 < 0.f && A1 < 0.f) { pt[nv] = at; px[nv] = ax; ++nv; }
-        // inside parameter intervals of the edge for each line
-        float a0 = 0.f, b0 = 1.f, a1 = 0.f, b1 = 1.f;
-        clip_param(A0, B0, a0, b0);
-        clip_param(A1, B1, a1, b1);
-        float s[2];
-        int ns = 0;
-        if ((A0 < 0.f) != (B0 < 0.f)) {
-            const float ss = cross_frac(A0, B0);
-            if (ss >= a1 && ss <= b1) s[ns++] = ss;
-        }
-        if ((A1 < 0.f) != (B1 < 0.f)) {
-            const float ss = cross_frac(A1, B1);
-            if (ss >= a0 && ss <= b0) s[ns++] = ss;
-        }
-        if (ns == 2 && s[1] < s[0]) { const float q = s[0]; s[0] = s[1]; s[1] = q; }
-        for (int q = 0; q < ns; ++q) {
-            pt[nv] = fmaf(s[q], bt - at, at);
-            px[nv] = fmaf(s[q], bx - ax, ax);
-            ++nv;
+        float ot[3], ox[3];
+        const int n = clip_square_edge(V, l0, l1, e, ot, ox);
+        for (int q = 0; q < n; ++q) {
+            if (nv < 8) {
+                pt[nv] = ot[q];
+                px[nv] = ox[q];
+                ++nv;
+            }
         }
     }
     return nv;

@@ -447,44 +447,188 @@ __device__ __forceinline__ void relaxed_voxels(const View& V, const Grid& G, con
     }
 }
 
-// H_n for detector column n, relaxed variant: its area and depth centroid into slot c.
-// Not inlined: it runs once per column and view.
-__device__ __noinline__ void build_column_cut(const View* Vp, const Column* Cp, float az, int n,
-                                              WarpSmemRelaxed* ws, int c) {
-    const View& V = *Vp;
-    const Column& C = *Cp;
+// The column cuts H_n, n = cstart + c (c < ncol <= KCT_CB), of one voxel column in one view
+// are built by the whole warp.
+//
+// Polygons: lanes 4c .. 4c + 3 clip the base square for column n, lane 4c + e taking square
+// edge e (clip_square_edge); the points are compacted, in the order of clip_square, into
+// (pts, pxs)[8c ..]. Each lane keeps its own points and returns whether its column exists.
+struct EdgePoints {
+    float t[3], x[3];
+    int n, first, nv;              // its points, their index in the polygon, the polygon's size
+};
+
+__device__ __forceinline__ bool clip_lanes(const View& V, const Column& C, int cstart, int ncol, int lane, float* pts,
+                                           float* pxs, EdgePoints& r) {
+    const int c = lane >> 2, e = lane & 3;
+    const bool act = c < ncol;
     Line lo, hi;
-    column_lines(V, C, n, lo, hi);
-    float* pt = ws->pt[c];
-    float* px = ws->px[c];
-    const int nv = clip_square(V, lo, hi, pt, px);
-    Green2 g{0.f, 0.f};
-    for (int e = 0; e < nv; ++e) {
-        const int f = (e + 1 == nv) ? 0 : e + 1;
-        seg_acc(g, pt[e], px[e], pt[f], px[f]);
+    column_lines(V, C, cstart + c, lo, hi);
+    r.n = act ? clip_square_edge(V, lo, hi, e, r.t, r.x) : 0;
+    int incl = r.n;
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+        const int t = __shfl_up_sync(FULLMASK, incl, o, 4);
+        if (e >= o) incl += t;
     }
-    const float m1 = 0.5f * g.a, mt = g.t * (1.f / 6.f);
-    const float tcm = m1 > 0.f ? mt * rcp_fast(m1) : 0.f;  // t' of the centre of mass of H_n
-    const float tn = C.tc + tcm, itn = rcp_fast(tn);
-    ws->fa[c] = make_float4(m1 * tn * V.inv_agv, tcm * itn, itn, 0.5f * az * fabsf(V.gv) * itn);
+    r.first = incl - r.n;
+    r.nv = min(__shfl_sync(FULLMASK, incl, 3, 4), 8);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        if (q < r.n && r.first + q < 8) {
+            pts[8 * c + r.first + q] = r.t[q];
+            pxs[8 * c + r.first + q] = r.x[q];
+        }
+    }
+    return act;
 }
 
-// H_n for detector column n, near-exact variant: its depth profile, moments and depth range
-// into slot c. Not inlined: it runs once per column and view.
-__device__ __noinline__ void build_column_cut(const View* Vp, const Column* Cp, float az, int n, WarpSmem* ws,
-                                              int c) {
+// Relaxed variant: the area of H_n and its depth centroid into slot c, the Green's-theorem
+// sums of each lane's edges added over the column's four lanes. Not inlined: it runs once
+// per column and view.
+__device__ __noinline__ void build_cuts(const View* Vp, const Column* Cp, float az, int cstart, int ncol, int lane,
+                                        WarpSmemRelaxed* ws) {
     const View& V = *Vp;
     const Column& C = *Cp;
-    Line lo, hi;
-    column_lines(V, C, n, lo, hi);
-    float* pt = ws->ev_p0 + 8 * c;     // scratch: the event queue is idle while cuts are built
-    float* px = ws->ev_p1 + 8 * c;
-    const int nv = clip_square(V, lo, hi, pt, px);
-    float g[5], tlo, thi;
-    depth_profile(pt, px, nv, ws->ivs[c], ws->iva[c], ws->ivb[c], ws->ivm[c], g, tlo, thi);
-    ws->fa[c] = make_float4(g[0], g[1], g[2], fmaf(C.tc, g[1], C.xc * g[3]));
-    ws->fb[c] = make_float4(fmaf(C.tc, g[2], C.xc * g[4]), tlo, thi, 0.f);
-    ws->fr[c] = make_float2(1.0f / (C.tc + tlo), 1.0f / (C.tc + thi));
+    EdgePoints r;
+    const bool act = clip_lanes(V, C, cstart, ncol, lane, &ws->pt[0][0], &ws->px[0][0], r);
+    __syncwarp();
+    const int c = lane >> 2;
+    Green2 g{0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int i = r.first + q;
+        if (q < r.n && i < r.nv) {
+            const int nx = i + 1 < r.nv ? i + 1 : 0;
+            seg_acc(g, r.t[q], r.x[q], ws->pt[c][nx], ws->px[c][nx]);
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+        g.a += __shfl_xor_sync(FULLMASK, g.a, o, 4);
+        g.t += __shfl_xor_sync(FULLMASK, g.t, o, 4);
+    }
+    if (act && (lane & 3) == 0) {
+        const float m1 = 0.5f * g.a, mt = g.t * (1.f / 6.f);
+        const float tcm = m1 > 0.f ? mt * rcp_fast(m1) : 0.f;  // t' of the centre of mass of H_n
+        const float tn = C.tc + tcm, itn = rcp_fast(tn);
+        ws->fa[c] = make_float4(m1 * tn * V.inv_agv, tcm * itn, itn, 0.5f * az * fabsf(V.gv) * itn);
+    }
+}
+
+// Near-exact variant: the depth profile of H_n (as depth_profile computes it serially), its
+// moments and depth range into slot c. After the polygons, lanes 8c' .. 8c' + 7 take column
+// c = c0 + c' and lane 8c' + v its vertex v: the chord of H_n at that vertex's depth T_v
+// (from every edge that spans it), and if the vertex is the first at the depth and below the
+// top, the interval from T_v to the next vertex depth (chord there from the lane of that
+// vertex) and its integral; the moments below T_v are the sum of the integrals of the
+// intervals below it, and the interval's index is their number. Not inlined: it runs once per
+// column and view.
+__device__ __noinline__ void build_cuts(const View* Vp, const Column* Cp, float az, int cstart, int ncol, int lane,
+                                        WarpSmem* ws) {
+    const View& V = *Vp;
+    const Column& C = *Cp;
+    int* nvs = reinterpret_cast<int*>(ws->ev_zs);     // scratch: the event queue is idle here
+    {
+        EdgePoints r;
+        const bool act = clip_lanes(V, C, cstart, ncol, lane, ws->ev_p0, ws->ev_p1, r);
+        if (act && (lane & 3) == 0) nvs[lane >> 2] = r.nv;
+    }
+    __syncwarp();
+    const int v = lane & 7, seg = lane & ~7;
+#pragma unroll 1
+    for (int c0 = 0; c0 < ncol; c0 += 4) {
+        const int c = c0 + (lane >> 3);
+        const bool colok = c < ncol;
+        const int nv = colok ? nvs[c] : 0;
+        const float* pt = ws->ev_p0 + 8 * c;
+        const float* px = ws->ev_p1 + 8 * c;
+        float T[8], X[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            T[u] = pt[u];          // slots u >= nv are not used
+            X[u] = px[u];
+        }
+        float tlo = 0.f, thi = 0.f;
+        if (nv > 0) {
+            tlo = 3.0e38f;
+            thi = -3.0e38f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (u < nv) {
+                    tlo = fminf(tlo, T[u]);
+                    thi = fmaxf(thi, T[u]);
+                }
+            }
+        }
+        const bool vert = v < nv;
+        const float Tv = vert ? pt[v] : 3.0e38f;
+        bool first = vert && nv >= 3;
+        float Tn = 3.0e38f;
+        int un = v;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (u < nv) {
+                if (u < v && T[u] == Tv) first = false;
+                if (T[u] > Tv && T[u] < Tn) {
+                    Tn = T[u];
+                    un = u;
+                }
+            }
+        }
+        // the chord at depth Tv (an edge along t' = Tv gives both of its ends)
+        float xl = 3.0e38f, xr = -3.0e38f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (u < nv) {
+                const bool wrap = u + 1 >= nv;
+                const float ta = T[u], xa = X[u], tb = wrap ? T[0] : T[(u + 1) & 7], xb = wrap ? X[0] : X[(u + 1) & 7];
+                if (fminf(ta, tb) <= Tv && Tv <= fmaxf(ta, tb)) {
+                    float x0 = xa, x1 = xb;
+                    if (ta != tb) x0 = x1 = fmaf((Tv - ta) * rcp_fast(tb - ta), xb - xa, xa);
+                    xl = fminf(xl, fminf(x0, x1));
+                    xr = fmaxf(xr, fmaxf(x0, x1));
+                }
+            }
+        }
+        const float w = vert ? fmaxf(xr - xl, 0.f) : 0.f, cm = vert ? 0.5f * (xl + xr) : 0.f;
+        const float wn = __shfl_sync(FULLMASK, w, seg + un), cn = __shfl_sync(FULLMASK, cm, seg + un);
+        const bool own = first && Tv < thi;   // the interval [Tv, Tn] is this lane's
+        float I[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        if (own) simpson5(Tv, Tn, Tn - Tv, 1.f, w, wn - w, cm, cn - cm, I[0], I[1], I[2], I[3], I[4]);
+        const unsigned ownm = (__ballot_sync(FULLMASK, own) >> seg) & 0xffu;
+        float B[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, S[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        int rank = 0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            float Iu[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) Iu[k] = __shfl_sync(FULLMASK, I[k], seg + u);
+            if ((ownm >> u) & 1u) {
+                const bool below = T[u] < Tv;
+                rank += below ? 1 : 0;
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    S[k] += Iu[k];
+                    if (below) B[k] += Iu[k];
+                }
+            }
+        }
+        if (colok) {
+            if (own) {
+                ws->ivs[c][rank] = Tv;
+                ws->iva[c][rank] = make_float4(rcp_fast(Tn - Tv), w, wn - w, cm);
+                ws->ivb[c][rank] = make_float4(cn - cm, B[0], B[1], B[2]);
+                ws->ivm[c][rank] = make_float2(B[3], B[4]);
+            }
+            if (v >= __popc(ownm)) ws->ivs[c][v] = 3.0e38f;
+            if (v == 0) {
+                ws->fa[c] = make_float4(S[0], S[1], S[2], fmaf(C.tc, S[1], C.xc * S[3]));
+                ws->fb[c] = make_float4(fmaf(C.tc, S[2], C.xc * S[4]), tlo, thi, 0.f);
+                ws->fr[c] = make_float2(1.0f / (C.tc + tlo), 1.0f / (C.tc + thi));
+            }
+        }
+    }
 }
 
 // All pairs of voxels kbase .. kbase + runs * SEG - 1 of column (i, j) in view V (in shared
@@ -502,7 +646,7 @@ __device__ __forceinline__ void warp_column(const View& V, const Grid& G, int i,
     for (int cstart = C.n_first; cstart <= C.n_last; cstart += KCT_CB) {
         const int ncol = min(KCT_CB, C.n_last - cstart + 1);
         __syncwarp();              // the previous readers of ws are done
-        if (lane < ncol) build_column_cut(&V, &C, G.az, cstart + lane, ws, lane);
+        build_cuts(&V, &C, G.az, cstart, ncol, lane, ws);
         __syncwarp();
 #pragma unroll 1
         for (int r = 0; r < runs; ++r) {
