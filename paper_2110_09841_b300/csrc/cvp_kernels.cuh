@@ -12,13 +12,14 @@
 //    the block writes each voxel once at the end.
 // Inside a block, a warp processes one voxel column at a time, lane l owning voxels
 // kbase + l + 32 p (p < KPL). The column cuts H_n of the voxel base are the same for every
-// voxel of the column (Sec. III-A, Eq. columnprojectionidentity): lane c computes H_n for
-// n = cstart + c and the warp shares the moments through shared memory. Each lane then
-// walks the rows of its own voxel. A row whose two planes stay inside the voxel over the
-// whole base gives its pairs in closed form from the moments of H_n; a plane that leaves the
-// voxel through its top or bottom face ("crossing") needs the moments of H_n cut at a depth
-// tau. Crossing planes are queued per warp and evaluated by all 32 lanes together, one
-// (event, column) task per lane, so the clipping never runs with most of the warp idle.
+// voxel of the column (Sec. III-A, Eq. columnprojectionidentity): the warp builds them
+// together (a few lanes per column) and shares their moments through shared memory. Each
+// lane then walks the rows of its own voxel. A row whose two planes stay inside the voxel
+// over the whole base gives its pairs in closed form from the moments of H_n; a plane that
+// leaves the voxel through its top or bottom face ("crossing") needs the moments of H_n cut
+// at a depth tau. The warp's crossing planes ("events") are numbered by a prefix sum over
+// the lanes and evaluated one per lane, each lane reading its event's plane from the owning
+// lane's registers, so the cuts never run with most of the warp idle.
 // Forward projection and adjoint enumerate the same pairs with the same code, so
 // <A x, y> = <x, A^T y> holds to float rounding.
 #pragma once
@@ -38,7 +39,7 @@ constexpr int NTHREADS = 32 * NWARP;
 // Blocks per SM: 2 for the near-exact kernels (their register need), 3 for the relaxed ones
 // (measured 21 % faster than with 2); the shared memory of a block (static part +
 // Brick::DYN_FLOATS floats) is sized accordingly.
-constexpr int EV_CAP = 64;         // crossing events queued per warp and round (>= KPL * KCT_ROWS)
+constexpr int EV_CAP = 64;         // crossing events evaluated per warp and round (>= KPL * KCT_ROWS)
 constexpr int KCT_ROWS = 32;       // row boundaries of one voxel (its footprint spans <= 31 rows)
 
 // Brick height along x_3: two runs of SEG voxels per column-cut build (the build is a large
@@ -68,8 +69,9 @@ struct WarpSmem {
     float4 fa[KCT_CB];             // exact: moments of H_n m1, mt, mtt, ml; relaxed: A_n, t_n, 1/t_n, -
     float4 fb[KCT_CB];             // exact: mlt, t'-range of H_n (lo, hi), -
     float2 fr[KCT_CB];             // exact: 1 / depth at the two ends of that range
-    float ev_p0[EV_CAP], ev_p1[EV_CAP], ev_zs[EV_CAP];
-    float res_v[EV_CAP], res_q[EV_CAP];
+    float res_v[EV_CAP], res_q[EV_CAP];   // exact: the crossing planes' region values (volume, moment)
+    float sc_t[KCT_CB * 8], sc_x[KCT_CB * 8];   // exact: vertices of H_n while the cuts are built
+    int sc_n[KCT_CB];
 };
 
 // The relaxed kernels keep only the column cuts' areas and depth centroids, so that their
@@ -105,6 +107,20 @@ __device__ __forceinline__ Mom cut_moments(const WarpSmem* ws, int c, float tau,
 // the same, not inlined, for the rare second cut of a plane that crosses both faces
 __device__ __noinline__ Mom cut_moments_call(const WarpSmem* ws, int c, float tau, float tc, float xc) {
     return cut_moments(ws, c, tau, tc, xc);
+}
+
+// position of set bit j (from 0, counted from the lowest) of m; j < popc(m)
+__device__ __forceinline__ int nth_bit(unsigned m, int j) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w; w >>= 1) {
+        const int c = __popc(m & ((1u << w) - 1u));   // set bits in the low half of the window
+        const bool up = j >= c;
+        j -= up ? c : 0;
+        m >>= up ? w : 0;
+        pos += up ? w : 0;
+    }
+    return pos;
 }
 
 // Volume and first moment along D of {(t', xi') in H_n, 0 < height < clamp(p0 + p1 t', 0, az)}
@@ -197,7 +213,7 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
         const F2 Bk = f2_axpy(B0, (float)k, dB);
         return ((((float)m - 0.5f) + Bk.hi) + Bk.lo) * C.da.hi;
     };
-    // the lane's voxels kbase + lane + 32 p; their crossing planes share one queue round
+    // the lane's voxels kbase + lane + 32 p; their crossing planes share one evaluation round
 #pragma unroll
     for (int p = 0; p < KPL; ++p) {
         const int k = kbase + p * 32 + lane;
@@ -269,7 +285,7 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
             base = incl - nl;
             total = __shfl_sync(FULLMASK, incl, 31);
         }
-        // lanes are served in contiguous groups whose events fit the queue (a lane has at
+        // lanes are served in contiguous groups whose events fit the result slots (a lane has at
         // most KPL * KCT_ROWS <= EV_CAP events, so every group makes progress)
         for (int lo_lane = 0; lo_lane < 32;) {
             int hi_lane = 32, e0 = 0;
@@ -280,45 +296,44 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
                 hi_lane = 32 - __clz(fit);
                 const int ne = __shfl_sync(FULLMASK, incl, hi_lane - 1) - base_lo;
                 e0 = base - base_lo;
-                // 1) queue the group's crossing planes (frame-transformed parameters)
-                if (lane >= lo_lane && lane < hi_lane && nl) {
-                    int ep = e0;
+                static_assert(KPL == 2, "the event decoding below reads the state of two voxels per lane");
+                // 1) lane e of the warp evaluates event e of the group (cut moments at the
+                // crossing depths): it is event j of lane s, the last lane whose events start
+                // at or before it, and its plane comes from that lane's state. A lane's events
+                // are, per voxel p, its crossing planes b <= rb in the bottom frame, then those
+                // b >= rb in the top frame.
+                const Mom full_m = Mom{fa.x, fa.y, fa.z, fa.w, fb.x};
+                const Mom zero_m = Mom{0.f, 0.f, 0.f, 0.f, 0.f};
+                for (int er = 0; er < ne; er += 32) {
+                    const int e = er + lane, target = base_lo + e;
+                    int src = 0;
 #pragma unroll
-                    for (int p = 0; p < KPL; ++p) {
-                        const int k = kbase + p * 32 + lane;
-                        const float zc = fmaf((float)k, az, G.z0) - V.sz;
-                        const float zs = zc * V.sgv;
-                        const float p1_0 = ((float)m_first[p] - 0.5f - V.cv) * V.inv_agv;
-                        const int rb = (R[p] + 1) >> 1;
-                        const unsigned mbot = cross[p] & ((2u << rb) - 1u), mtop = cross[p] & ~((1u << rb) - 1u);
-                        const int nbot = __popc(mbot);
-                        for (unsigned m = cross[p]; m; m &= m - 1u) {
-                            const int b = __ffs(m) - 1;
-                            const float p0 = fmaf(0.5f, az, fmaf((float)b, dp0, off0p[p])), p1 = fmaf((float)b, dp1, p1_0);
-                            if (b <= rb) {
-                                const int q = ep + __popc(mbot & ((1u << b) - 1u));
-                                ws->ev_p0[q] = p0;
-                                ws->ev_p1[q] = p1;
-                                ws->ev_zs[q] = zs;
-                            }
-                            if (b >= rb) {
-                                const int q = ep + nbot + __popc(mtop & ((1u << b) - 1u));
-                                ws->ev_p0[q] = az - p0;
-                                ws->ev_p1[q] = -p1;
-                                ws->ev_zs[q] = -zs;
-                            }
-                        }
-                        ep += nev[p];
-                    }
-                }
-                __syncwarp();
-                // 2) the whole warp evaluates the events (cut moments at the crossing depths)
-                for (int e = lane; e < ne; e += 32) {
-                    const float p0 = ws->ev_p0[e], p1 = ws->ev_p1[e];
+                    for (int step = 16; step; step >>= 1)
+                        if (__shfl_sync(FULLMASK, base, src + step) <= target) src += step;
+                    int j = target - __shfl_sync(FULLMASK, base, src);
+                    const unsigned cm0 = __shfl_sync(FULLMASK, cross[0], src), cm1 = __shfl_sync(FULLMASK, cross[1], src);
+                    const int rr0 = __shfl_sync(FULLMASK, R[0], src), rr1 = __shfl_sync(FULLMASK, R[1], src);
+                    const int mf0 = __shfl_sync(FULLMASK, m_first[0], src), mf1 = __shfl_sync(FULLMASK, m_first[1], src);
+                    const float of0 = __shfl_sync(FULLMASK, off0p[0], src), of1 = __shfl_sync(FULLMASK, off0p[1], src);
+                    if (e >= ne) continue;
+                    // the event's voxel p, frame and plane b
+                    const int rb0 = (rr0 + 1) >> 1, rb1 = (rr1 + 1) >> 1;
+                    const unsigned mb0 = cm0 & ((2u << rb0) - 1u), mt0 = cm0 & ~((1u << rb0) - 1u);
+                    const unsigned mb1 = cm1 & ((2u << rb1) - 1u), mt1 = cm1 & ~((1u << rb1) - 1u);
+                    const int n0 = __popc(mb0), n1 = n0 + __popc(mt0), n2 = n1 + __popc(mb1);
+                    const bool p1v = j >= n1, top = (j >= n0 && j < n1) || j >= n2;
+                    const unsigned msk = j < n0 ? mb0 : j < n1 ? mt0 : j < n2 ? mb1 : mt1;
+                    const int jj = j - (j < n0 ? 0 : j < n1 ? n0 : j < n2 ? n1 : n2);
+                    const int b = nth_bit(msk, jj);
+                    const int k = kbase + (p1v ? 32 : 0) + src;
+                    const float zc = fmaf((float)k, az, G.z0) - V.sz;
+                    const float zs0 = zc * V.sgv;
+                    const float p1_0 = ((float)(p1v ? mf1 : mf0) - 0.5f - V.cv) * V.inv_agv;
+                    const float q0 = fmaf(0.5f, az, fmaf((float)b, dp0, p1v ? of1 : of0)), q1 = fmaf((float)b, dp1, p1_0);
+                    const float p0 = top ? az - q0 : q0, p1 = top ? -q1 : q1, zs = top ? -zs0 : zs0;
                     const float p1s = (fabsf(p1) < 1e-30f) ? copysignf(1e-30f, p1) : p1;
-                    const Mom full_m = Mom{fa.x, fa.y, fa.z, fa.w, fb.x};
-                    const float tau0 = -p0 / p1s, tau1 = (az - p0) / p1s;
-                    const Mom zero_m = Mom{0.f, 0.f, 0.f, 0.f, 0.f};
+                    const float ip1 = rcp_fast(p1s);
+                    const float tau0 = -p0 * ip1, tau1 = (az - p0) * ip1;
                     // A plane usually leaves through one face only, so one of the two depths
                     // lies inside H_n's depth range: one call site serves every lane (a
                     // second one only for planes that cross both faces within H_n).
@@ -329,7 +344,7 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
                     const Mom c0 = in0 ? ca : (tau0 <= tlo) ? zero_m : full_m;
                     const Mom c1 = in1 ? (in0 ? cb : ca) : (tau1 <= tlo) ? zero_m : full_m;
                     float gv, gq;
-                    g_cross_from(az, c0, c1, full_m, p0, p1, p1s, ws->ev_zs[e], gv, gq);
+                    g_cross_from(az, c0, c1, full_m, p0, p1, p1s, zs, gv, gq);
                     ws->res_v[e] = gv;
                     ws->res_q[e] = gq;
                 }
@@ -423,7 +438,7 @@ __device__ __forceinline__ void relaxed_voxels(const View& V, const Grid& G, con
         if (k >= G.nz) continue;
         sink.begin(pass, k);
         const float zc = fmaf((float)k, az, G.z0) - V.sz;
-        const float iD2 = 1.0f / fmaf(C.tc, C.tc, fmaf(C.xc, C.xc, zc * zc));
+        const float iD2 = rcp_fast(fmaf(C.tc, C.tc, fmaf(C.xc, C.xc, zc * zc)));
         const float gz = V.gv * zc;
         const F2 Bk = f2_axpy(B0, (float)k, dB);
         const float bs = Bk.hi, bl = Bk.lo, vch = -(bs + V.cv);
@@ -528,10 +543,10 @@ __device__ __noinline__ void build_cuts(const View* Vp, const Column* Cp, float 
                                         WarpSmem* ws) {
     const View& V = *Vp;
     const Column& C = *Cp;
-    int* nvs = reinterpret_cast<int*>(ws->ev_zs);     // scratch: the event queue is idle here
+    int* nvs = ws->sc_n;
     {
         EdgePoints r;
-        const bool act = clip_lanes(V, C, cstart, ncol, lane, ws->ev_p0, ws->ev_p1, r);
+        const bool act = clip_lanes(V, C, cstart, ncol, lane, ws->sc_t, ws->sc_x, r);
         if (act && (lane & 3) == 0) nvs[lane >> 2] = r.nv;
     }
     __syncwarp();
@@ -541,8 +556,8 @@ __device__ __noinline__ void build_cuts(const View* Vp, const Column* Cp, float 
         const int c = c0 + (lane >> 3);
         const bool colok = c < ncol;
         const int nv = colok ? nvs[c] : 0;
-        const float* pt = ws->ev_p0 + 8 * c;
-        const float* px = ws->ev_p1 + 8 * c;
+        const float* pt = ws->sc_t + 8 * c;
+        const float* px = ws->sc_x + 8 * c;
         float T[8], X[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
