@@ -41,14 +41,14 @@ UNIT = "Gvoxel·views/s"
 # per view, the adjoint reads one projection tile per view and writes the volume once, so
 # traffic is scaled as below.
 NCU = {
-    "exact project": {"flop_per_vv": 887.3, "warp_per_vv": 94.8, "simt": 0.67,
-                      "dram_read_8": 5.77e8, "dram_write_8": 3.13e7},
-    "exact backproject": {"flop_per_vv": 957.2, "warp_per_vv": 99.6, "simt": 0.69,
-                          "dram_read_8": 5.92e7, "dram_write_8": 4.93e8},
-    "relaxed project": {"flop_per_vv": 187.0, "warp_per_vv": 26.6, "simt": 0.66,
-                        "dram_read_8": 5.79e8, "dram_write_8": 3.29e7},
-    "relaxed backproject": {"flop_per_vv": 232.1, "warp_per_vv": 36.3, "simt": 0.61,
-                            "dram_read_8": 5.34e7, "dram_write_8": 4.98e8},
+    "exact project": {"flop_per_vv": 794.2, "warp_per_vv": 80.6, "simt": 0.78,
+                      "dram_read_8": 5.75e8, "dram_write_8": 3.02e7},
+    "exact backproject": {"flop_per_vv": 880.5, "warp_per_vv": 86.5, "simt": 0.80,
+                          "dram_read_8": 5.63e7, "dram_write_8": 4.90e8},
+    "relaxed project": {"flop_per_vv": 186.1, "warp_per_vv": 23.6, "simt": 0.77,
+                        "dram_read_8": 5.70e8, "dram_write_8": 2.91e7},
+    "relaxed backproject": {"flop_per_vv": 233.9, "warp_per_vv": 30.3, "simt": 0.77,
+                            "dram_read_8": 4.55e7, "dram_write_8": 4.89e8},
 }
 
 

@@ -138,17 +138,8 @@ KCT_HD void g_cross_from(float az, const Mom& c0, const Mom& c1, const Mom& full
     gq = fmaf(zs, fmaf(0.5f, Sh2, -0.5f * az * Vg), Sl);
 }
 
-// the same quantity for a plane that stays inside the voxel over the whole base
-KCT_HD void g_lin(float az, float p0, float p1, float zs, float f1, float ft, float ftt, float fl, float flt,
-                  float& gv, float& gq) {
-    const float Vg = fmaf(p0, f1, p1 * ft);
-    const float Sl = fmaf(p0, fl, p1 * flt);
-    const float Sh2 = fmaf(p0 * p0, f1, fmaf(2.f * p0 * p1, ft, p1 * p1 * ftt));
-    gv = Vg;
-    gq = fmaf(zs, fmaf(0.5f, Sh2, -0.5f * az * Vg), Sl);
-}
-
-// g_lin with paired FP32 instructions (two independent FMAs per issue)
+// the same quantity for a plane that stays inside the voxel over the whole base, with paired
+// FP32 instructions (two independent FMAs per issue)
 __device__ __forceinline__ void g_lin2(float az, float p0, float p1, float zs, float f1, float ft, float ftt, float fl,
                                        float flt, float& gv, float& gq) {
     const float2 vs = __ffma2_rn(make_float2(p0, p0), make_float2(f1, fl), __fmul2_rn(make_float2(p1, p1), make_float2(ft, flt)));
