@@ -193,6 +193,12 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
                                              int kbase, int lane, WarpSmem* ws, Sink& sink, int* err) {
     const float az = G.az, agv = fabsf(V.gv);
     const float dp0 = C.tc * V.inv_agv, dp1 = V.inv_agv;   // change of p0, p1 from one row boundary to the next
+    const float idp0 = agv * C.itc;                         // 1 / dp0
+    // Rows r < rb take the bottom frame, the others the top frame. Plane rb is the one nearest
+    // the voxel's mid-height at the column centre (p0 = az/2): its value passes from one frame
+    // to the other as the complement az (m1, ml) - g, which loses nothing there, and every
+    // other plane is evaluated in the frame of the face it is nearer to.
+    auto frame_split = [&](float off0, int R) { return max(1, min(R, __float2int_rn(-off0 * idp0))); };
     const float vtiny = 1e-9f * G.ax * G.ay * az;
     // Height offset of row boundary m - 1/2 over the centre of voxel k at the column centre depth,
     // tc (m - 1/2 - v_c) / |gv| = ((m - 1/2) + B_k) da (row_frame): the row distance is formed in
@@ -258,9 +264,8 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
             cross[p] = cr;
             zero[p] = ze;
             full[p] = fu;
-            const int rb = (R[p] + 1) >> 1;                     // rows r < rb use the bottom frame
-            // planes b <= rb give a bottom-frame event, b >= rb a top-frame one
-            nev[p] = __popc(cr & ((2u << rb) - 1u)) + __popc(cr & ~((1u << rb) - 1u));
+            // planes b <= rb give a bottom-frame event, b > rb a top-frame one
+            nev[p] = __popc(cr);
         }
         int nl = 0;
 #pragma unroll
@@ -292,7 +297,7 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
                 // crossing depths): it is event j of lane s, the last lane whose events start
                 // at or before it, and its plane comes from that lane's state. A lane's events
                 // are, per voxel p, its crossing planes b <= rb in the bottom frame, then those
-                // b >= rb in the top frame.
+                // b > rb in the top frame.
                 const Mom full_m = Mom{fa.x, fa.y, fa.z, fa.w, fb.x};
                 const Mom zero_m = Mom{0.f, 0.f, 0.f, 0.f, 0.f};
                 for (int er = 0; er < ne; er += 32) {
@@ -308,9 +313,9 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
                     const float of0 = __shfl_sync(FULLMASK, off0p[0], src), of1 = __shfl_sync(FULLMASK, off0p[1], src);
                     if (e >= ne) continue;
                     // the event's voxel p, frame and plane b
-                    const int rb0 = (rr0 + 1) >> 1, rb1 = (rr1 + 1) >> 1;
-                    const unsigned mb0 = cm0 & ((2u << rb0) - 1u), mt0 = cm0 & ~((1u << rb0) - 1u);
-                    const unsigned mb1 = cm1 & ((2u << rb1) - 1u), mt1 = cm1 & ~((1u << rb1) - 1u);
+                    const int rb0 = frame_split(of0, rr0), rb1 = frame_split(of1, rr1);
+                    const unsigned mb0 = cm0 & ((2u << rb0) - 1u), mt0 = cm0 & ~((2u << rb0) - 1u);
+                    const unsigned mb1 = cm1 & ((2u << rb1) - 1u), mt1 = cm1 & ~((2u << rb1) - 1u);
                     const int n0 = __popc(mb0), n1 = n0 + __popc(mt0), n2 = n1 + __popc(mb1);
                     const bool p1v = j >= n1, top = (j >= n0 && j < n1) || j >= n2;
                     const unsigned msk = j < n0 ? mb0 : j < n1 ? mt0 : j < n2 ? mb1 : mt1;
@@ -352,13 +357,13 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
                     const float zs = zc * V.sgv;
                     const float D2 = fmaf(C.tc, C.tc, fmaf(C.xc, C.xc, zc * zc));
                     const float p1_0 = ((float)m_first[p] - 0.5f - V.cv) * V.inv_agv;
-                    const int rb = (R[p] + 1) >> 1;
-                    const unsigned mbot = cross[p] & ((2u << rb) - 1u), mtop = cross[p] & ~((1u << rb) - 1u);
+                    const int rb = frame_split(off0p[p], R[p]);
+                    const unsigned mbot = cross[p] & ((2u << rb) - 1u), mtop = cross[p] & ~((2u << rb) - 1u);
                     const int nbot = __popc(mbot);
                     // Every row is the difference of its two planes' region values in the row's frame
                     // (bottom for r < rb, top after), so all lanes take the same path whatever the
                     // planes' classes; the upper plane's value is carried to the next row, whose
-                    // lower plane it is (recomputed where the frame changes).
+                    // lower plane it is (complemented where the frame changes).
                     float carry_v = 0.f, carry_q = 0.f;
 #pragma unroll 1
                     for (int r = 0; r < R[p]; ++r) {
@@ -367,9 +372,10 @@ __device__ __forceinline__ void exact_voxels(const View& V, const Grid& G, const
                         {
                             const bool top = r >= rb;
                             float g[2][2];
-                            const bool reuse = r > 0 && r != rb;
-                            g[0][0] = carry_v;
-                            g[0][1] = carry_q;
+                            const bool reuse = r > 0;
+                            // plane rb changes frame: its value from the other face
+                            g[0][0] = r == rb ? fmaf(az, fa.x, -carry_v) : carry_v;
+                            g[0][1] = r == rb ? fmaf(az, fa.w, -carry_q) : carry_q;
 #pragma unroll
                             for (int h = 0; h < 2; ++h) {
                                 if (h == 0 && reuse) continue;
