@@ -41,12 +41,12 @@ UNIT = "Gvoxel·views/s"
 # per view, the adjoint reads one projection tile per view and writes the volume once, so
 # traffic is scaled as below.
 NCU = {
-    "exact project": {"flop_per_vv": 794.2, "warp_per_vv": 80.6, "simt": 0.78,
-                      "dram_read_8": 5.75e8, "dram_write_8": 3.02e7},
-    "exact backproject": {"flop_per_vv": 880.5, "warp_per_vv": 86.5, "simt": 0.80,
-                          "dram_read_8": 5.63e7, "dram_write_8": 4.90e8},
+    "exact project": {"flop_per_vv": 732.6, "warp_per_vv": 79.6, "simt": 0.78,
+                      "dram_read_8": 5.75e8, "dram_write_8": 3.01e7},
+    "exact backproject": {"flop_per_vv": 818.2, "warp_per_vv": 84.6, "simt": 0.80,
+                          "dram_read_8": 5.23e7, "dram_write_8": 4.89e8},
     "relaxed project": {"flop_per_vv": 186.1, "warp_per_vv": 23.6, "simt": 0.77,
-                        "dram_read_8": 5.70e8, "dram_write_8": 2.91e7},
+                        "dram_read_8": 5.71e8, "dram_write_8": 2.93e7},
     "relaxed backproject": {"flop_per_vv": 233.9, "warp_per_vv": 30.3, "simt": 0.77,
                             "dram_read_8": 4.55e7, "dram_write_8": 4.89e8},
 }
