@@ -633,7 +633,11 @@ int or_backproject_voxels(int nx, int ny, int nz, double ax, double ay, double a
 /* Forward projection of selected pixels only. pix: [count][3] = (view, v, u).
  * Candidate voxels: columns (i, j) whose base square is not entirely outside one of
  * the two column planes of the pixel, and for those the slices k that meet the z-range
- * of the row slab over the column's four vertical edges. */
+ * of the row slab over the column's four vertical edges.
+ * variant 0 / 1: the near-exact / relaxed pair weights W; variant 2: the truth integral
+ * J = int_cut r^-2 dV of every pair (Eq. intcut) in place of W, so that with the exact
+ * scaling the pixel value is the solid-angle average over the pixel of the line integrals
+ * of the voxel volume (Eq. integub), with no sampling of rays. */
 int or_project_pixels(int nx, int ny, int nz, double ax, double ay, double az, int nu, int nv,
                       const double *pmats, int nviews, int variant, int scaling,
                       const double *x, const int32_t *pix, int count, double *out) {
@@ -681,8 +685,8 @@ int or_project_pixels(int nx, int ny, int nz, double ax, double ay, double az, i
                     double lo[3], hi[3];
                     voxel_box(&G, i, j, k, lo, hi);
                     pair_t p;
-                    box_pixel_pair(&V, lo, hi, pu, pv, 0, &p);
-                    acc += mu * pair_weight(&p, variant);
+                    box_pixel_pair(&V, lo, hi, pu, pv, variant == 2 ? 1 : 0, &p);
+                    acc += mu * (variant == 2 ? p.J : pair_weight(&p, variant));
                 }
             }
         out[q] = acc * pixel_factor(&V, pu, pv, scaling);

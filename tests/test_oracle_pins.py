@@ -252,6 +252,45 @@ def test_centroid_weight_vs_exact_integral():
                     assert abs(q["W"] - q["J"]) <= 3.0 / r2 * q["J"]
 
 
+def test_truth_integrals_add_up_to_the_voxel_integral():
+    """The truth mode of the sampled projection (J = int_cut r^-2 dV per pair, Eq. intcut)
+    summed over a voxel's pixels is the voxel's whole int r^-2 dV, here by tensor
+    Gauss-Legendre (the pixel factor divided out); the centroid weight W differs from it
+    by O((a / r)^2), so a truth mode that fell back to W would fail."""
+    g = small_geometry(n=(5, 5, 5), a=(1.0, 0.8, 1.3), det=(40, 40), pitch=(0.7, 0.6))
+    for view in (0, 3):
+        P = g.pmats[view]
+        for (i, j, k) in [(0, 0, 0), (2, 2, 2), (4, 1, 3)]:
+            lo, hi, _ = voxel_bounds(g, i, j, k)
+            u0, u1, v0, v1, inside = footprint(P, lo, hi, g.nu, g.nv)
+            assert inside
+            x = np.zeros(g.vol_shape)
+            x[k, j, i] = 1.0
+            pix = np.array([[view, v, u] for u in range(u0, u1 + 1) for v in range(v0, v1 + 1)])
+            F = np.array([oracle.pixel_factor(P, u, v, oracle.SCALE_EXACT) for _, v, u in pix])
+            t = oracle.project_pixels(g, x, pix, oracle.TRUTH, oracle.SCALE_EXACT) / F
+            w = oracle.project_pixels(g, x, pix, oracle.EXACT, oracle.SCALE_EXACT) / F
+            ref = gauss_legendre_box(lo, hi, oracle.source(P), n=12, split=2)
+            assert t.sum() == pytest.approx(ref, rel=1e-12)
+            assert abs(w.sum() / ref - 1.0) > 1e-7
+
+
+def test_truth_mode_is_the_limit_of_ray_integration():
+    """With the exact scaling the truth mode is the solid-angle average over the pixel of
+    the line integrals (Eq. integub with Eq. intcut): K x K solid-angle weighted rays with
+    exact path lengths converge to it, closer than to the near-exact value W."""
+    g = small_geometry(n=(4, 4, 4), det=(24, 20), pitch=(0.4, 0.4), nviews=3, sid=200.0, sdd=300.0)
+    x = np.random.default_rng(5).uniform(0.5, 1.5, g.vol_shape)
+    for view, u, v, tol in [(0, 12, 10, 1e-9), (1, 10, 8, 1e-7), (2, 13, 11, 1e-7), (1, 19, 16, 1e-8),
+                            (0, 4, 3, 2e-5)]:     # the last pixel sees a corner of the volume
+        pix = np.array([[view, v, u]])
+        t = oracle.project_pixels(g, x, pix, oracle.TRUTH, oracle.SCALE_EXACT)[0]
+        w = oracle.project_pixels(g, x, pix, oracle.EXACT, oracle.SCALE_EXACT)[0]
+        r = oracle.ray_pixel(g, x, view, u, v, 256, weighting=1)
+        assert abs(r / t - 1.0) <= tol
+        assert abs(r - t) < abs(r - w)
+
+
 def test_single_voxel_in_one_big_pixel():
     """P5: a voxel wholly inside one pixel gives W = a^3 / |c - s|^2 and J equals the
     tensor Gauss-Legendre integral of r^-2 over the box."""
