@@ -43,6 +43,11 @@
  * Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
  * kct_project and kct_backproject enqueue work only: they allocate nothing, do not
  * synchronise and may be captured in a CUDA graph.
+ *
+ * Devices: a plan belongs to the device that was current when it was created. Every call
+ * that takes a plan makes that device current while it runs and gives the calling thread
+ * its previous current device back before returning; `stream` must belong to the plan's
+ * device.
  */
 #ifndef KCT_H
 #define KCT_H

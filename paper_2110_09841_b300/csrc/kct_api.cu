@@ -219,15 +219,24 @@ double brick_overflow(const double* pmats, int nviews, const kct_volume_desc& vo
     return count ? (double)over / count : 0.0;
 }
 
-// opt in to more than 48 KB of shared memory per block (once per process)
+constexpr int kMaxDevices = 64;
+
+// opt in to more than 48 KB of shared memory per block (once per device: the attribute
+// belongs to the kernel on the current device)
 template <class K>
 cudaError_t set_dyn(K kernel, size_t bytes, cudaError_t e) {
     return e == cudaSuccess ? cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) : e;
 }
 
 cudaError_t brick_kernel_attributes() {
-    static cudaError_t done = [] {
-        cudaError_t e = cudaSuccess;
+    static std::mutex mu;
+    static bool done[kMaxDevices] = {};
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!done[dev]) {
         e = set_dyn(kct::fwd_kernel<0, 0>, brick_dyn_smem<0>(), e);
         e = set_dyn(kct::fwd_kernel<0, 1>, brick_dyn_smem<0>(), e);
         e = set_dyn(kct::fwd_kernel<1, 0>, brick_dyn_smem<1>(), e);
@@ -240,9 +249,9 @@ cudaError_t brick_kernel_attributes() {
         e = set_dyn(kct::bwd_kernel<1, 1>, brick_dyn_smem<1, false>(), e);
         e = set_dyn(kct::bwd_kernel<1, 0, 2>, brick_dyn_smem<1, false, 2>(), e);
         e = set_dyn(kct::bwd_kernel<1, 1, 2>, brick_dyn_smem<1, false, 2>(), e);
-        return e;
-    }();
-    return done;
+        done[dev] = e == cudaSuccess;
+    }
+    return e;
 }
 
 unsigned view_chunks(const Grid& G, int chunk) { return (unsigned)((G.nviews + chunk - 1) / chunk); }
@@ -300,16 +309,29 @@ kct_status check_plan(const kct_plan* p) {
     return KCT_OK;
 }
 
-kct_status set_device(const kct_plan* p) {
-    int cur = -1;
-    cudaError_t e = cudaGetDevice(&cur);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    if (cur != p->device) {
-        e = cudaSetDevice(p->device);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+// Makes the plan's device current for the duration of one call and gives the calling thread
+// its previous device back on return (the work enqueued stays on its stream).
+class DeviceScope {
+  public:
+    explicit DeviceScope(int dev) {
+        err_ = cudaGetDevice(&prev_);
+        if (err_ == cudaSuccess && prev_ != dev) {
+            err_ = cudaSetDevice(dev);
+            switched_ = err_ == cudaSuccess;
+        }
     }
-    return KCT_OK;
-}
+    ~DeviceScope() {
+        if (switched_) cudaSetDevice(prev_);
+    }
+    DeviceScope(const DeviceScope&) = delete;
+    DeviceScope& operator=(const DeviceScope&) = delete;
+    kct_status status() const { return err_ == cudaSuccess ? KCT_OK : cuda_fail(err_, "selecting the plan's device"); }
+
+  private:
+    int prev_ = -1;
+    bool switched_ = false;
+    cudaError_t err_ = cudaSuccess;
+};
 
 }  // namespace
 
@@ -435,7 +457,8 @@ static kct_status project_impl(const kct_plan* p, const float* d_vol, float* d_p
     const Grid& G = p->grid;
     if ((long long)view_chunks(G, p->fwd_chunk) * nbatch > 65535)
         return fail(KCT_ERR_UNSUPPORTED, "batch too large for one launch");
-    if ((s = set_device(p)) != KCT_OK) return s;
+    DeviceScope scope(p->device);
+    if ((s = scope.status()) != KCT_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     size_t pbytes = sizeof(float) * (size_t)G.nu * G.nv * G.nviews * nbatch;
     cudaError_t e;
@@ -461,7 +484,8 @@ static kct_status backproject_impl(const kct_plan* p, const float* d_proj, float
     if (s != KCT_OK) return s;
     if (!d_vol || !d_proj) return fail(KCT_ERR_INVALID_ARG, "null data pointer");
     if (nbatch <= 0 || nbatch > 65535) return fail(KCT_ERR_INVALID_ARG, "nbatch must be in [1, 65535]");
-    if ((s = set_device(p)) != KCT_OK) return s;
+    DeviceScope scope(p->device);
+    if ((s = scope.status()) != KCT_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     const int key = (p->variant == KCT_CVP_RELAXED ? 2 : 0) + (p->scaling == KCT_SCALE_EXACT ? 1 : 0);
     const int acc = accumulate ? 1 : 0;
@@ -515,7 +539,8 @@ kct_status kct_plan_autotune(kct_plan* p, const float* d_vol, float* d_proj, int
     kct_status s = check_plan(p);
     if (s != KCT_OK) return s;
     if (!d_vol || !d_proj) return fail(KCT_ERR_INVALID_ARG, "null data pointer");
-    if ((s = set_device(p)) != KCT_OK) return s;
+    DeviceScope scope(p->device);
+    if ((s = scope.status()) != KCT_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     Grid G = p->grid;
     G.nviews = std::min(G.nviews, kct::TUNE_VIEWS);
@@ -559,7 +584,8 @@ kct_status kct_siddon_project(const kct_plan* p, const float* d_vol, float* d_pr
     if (s != KCT_OK) return s;
     if (!d_vol || !d_proj) return fail(KCT_ERR_INVALID_ARG, "null data pointer");
     if (K < 1 || K > 64) return fail(KCT_ERR_INVALID_ARG, "K must be in [1, 64]");
-    if ((s = set_device(p)) != KCT_OK) return s;
+    DeviceScope scope(p->device);
+    if ((s = scope.status()) != KCT_OK) return s;
     const Grid& G = p->grid;
     const long long npix = (long long)G.nu * G.nv;
     dim3 grid((unsigned)((npix + 7) / 8), (unsigned)G.nviews);
@@ -574,7 +600,8 @@ kct_status kct_pixel_factors(const kct_plan* p, float* d_out, void* stream) {
     kct_status s = check_plan(p);
     if (s != KCT_OK) return s;
     if (!d_out) return fail(KCT_ERR_INVALID_ARG, "null output pointer");
-    if ((s = set_device(p)) != KCT_OK) return s;
+    DeviceScope scope(p->device);
+    if ((s = scope.status()) != KCT_OK) return s;
     const Grid& G = p->grid;
     long n = (long)G.nu * G.nv;
     dim3 grid((unsigned)((n + 255) / 256), G.nviews);
@@ -591,7 +618,8 @@ kct_status kct_count_pairs(const kct_plan* p, uint64_t* count, void* stream) {
     kct_status s = check_plan(p);
     if (s != KCT_OK) return s;
     if (!count) return fail(KCT_ERR_INVALID_ARG, "null output pointer");
-    if ((s = set_device(p)) != KCT_OK) return s;
+    DeviceScope scope(p->device);
+    if ((s = scope.status()) != KCT_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(p->d_count, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
@@ -611,7 +639,8 @@ kct_status kct_last_device_error(const kct_plan* p, int32_t* code, void* stream)
     kct_status s = check_plan(p);
     if (s != KCT_OK) return s;
     if (!code) return fail(KCT_ERR_INVALID_ARG, "null output pointer");
-    if ((s = set_device(p)) != KCT_OK) return s;
+    DeviceScope scope(p->device);
+    if ((s = scope.status()) != KCT_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     int h = 0;
     cudaError_t e = cudaMemcpyAsync(&h, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -667,7 +696,8 @@ kct_status kct_cgls(const kct_plan* p, const float* d_b, float* d_x, const float
     if (work_bytes < L.total) return fail(KCT_ERR_INVALID_ARG, "workspace smaller than kct_cgls_workspace_bytes");
     if (((uintptr_t)d_work & 255) || ((uintptr_t)d_b & 15) || ((uintptr_t)d_x & 15) || ((uintptr_t)d_atb & 15))
         return fail(KCT_ERR_INVALID_ARG, "d_work must be 256-byte and d_b, d_x, d_atb 16-byte aligned");
-    if ((s = set_device(p)) != KCT_OK) return s;
+    DeviceScope scope(p->device);
+    if ((s = scope.status()) != KCT_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     int sms = 0;
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
@@ -770,7 +800,6 @@ constexpr size_t kStaticBytes = kStaticSumOffset + kStaticSums * sizeof(float); 
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_static_mutex;
 void* g_static_ptr[kMaxDevices];
 

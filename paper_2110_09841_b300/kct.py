@@ -144,11 +144,14 @@ class Projector:
 
     geom: paper_2110_09841_b300.inputs.Geometry (voxel grid, detector, float64 [V,3,4] matrices).
     variant: "exact" | "relaxed";  scaling: "cos" | "exact".
-    The plan lives on the current CUDA device.
+    The plan lives on the CUDA device current at construction (`self.device`).
     """
 
     def __init__(self, geom, variant="exact", scaling="cos"):
+        import torch
+
         self.lib = load()
+        self.device = torch.device("cuda", torch.cuda.current_device())
         self.geom = geom
         self.variant = _VARIANTS[variant]
         self.scaling = _SCALINGS[scaling]
@@ -257,7 +260,7 @@ class Projector:
         """Device scratch for cgls(): a uint8 CUDA tensor of kct_cgls_workspace_bytes."""
         import torch
 
-        return torch.empty(int(self.lib.kct_cgls_workspace_bytes(self._h)), dtype=torch.uint8, device="cuda")
+        return torch.empty(int(self.lib.kct_cgls_workspace_bytes(self._h)), dtype=torch.uint8, device=self.device)
 
     def cgls(self, b, x0=None, max_iter=100, tol=1e-3, out=None, workspace=None, atb=None, stream=None):
         """CGLS for min |b - A x| (kct_cgls): from x0 (warm start) or from 0, until the
@@ -305,7 +308,7 @@ class Projector:
     def pixel_factors(self, stream=None):
         import torch
 
-        out = torch.empty(self.geom.proj_shape, dtype=torch.float32, device="cuda")
+        out = torch.empty(self.geom.proj_shape, dtype=torch.float32, device=self.device)
         _check(self.lib.kct_pixel_factors(self._h, ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
         return out
 
