@@ -246,6 +246,46 @@ static double ptope_inv_r2(const ptope_t *P, v3 s, int level) {
     return J;
 }
 
+/* int_T |x - s| / |m2 . (x - s)|^3 dA over triangle T, split into 4^level sub-triangles */
+static double tri_area_kernel(v3 a, v3 b, v3 c, v3 s, v3 m2, int level) {
+    if (level > 0) {
+        v3 ab = scl(add(a, b), 0.5), bc = scl(add(b, c), 0.5), ca = scl(add(c, a), 0.5);
+        return tri_area_kernel(a, ab, ca, s, m2, level - 1) + tri_area_kernel(ab, b, bc, s, m2, level - 1) +
+               tri_area_kernel(ca, bc, c, s, m2, level - 1) + tri_area_kernel(ab, bc, ca, s, m2, level - 1);
+    }
+    double B[7][3], w[7];
+    tri_rule(B, w);
+    double area = 0.5 * norm(cross(sub(b, a), sub(c, a)));
+    double acc = 0.0;
+    for (int q = 0; q < 7; ++q) {
+        v3 p = add(add(scl(a, B[q][0]), scl(b, B[q][1])), scl(c, B[q][2]));
+        v3 r = sub(p, s);
+        double t = fabs(dot(m2, r));
+        acc += w[q] * norm(r) / (t * t * t);
+    }
+    return acc * area;
+}
+
+/* int_P |x - s| / |m2 . (x - s)|^3 dV = sum_faces h_F int_F |x - s| / |m2 . (x - s)|^3 dA: the
+ * field (x - s) |x - s| / |m2 . (x - s)|^3 is homogeneous of degree -2 about s, so its
+ * divergence is the integrand, as for |x - s|^-2 above. */
+static double ptope_area_kernel(const ptope_t *P, v3 s, v3 m2, int level) {
+    double K = 0.0;
+    for (int f = 0; f < P->nf; ++f) {
+        const face_t *F = &P->f[f];
+        v3 nrm = mk(0, 0, 0);
+        for (int k = 1; k + 1 < F->nv; ++k)
+            nrm = add(nrm, cross(sub(F->v[k], F->v[0]), sub(F->v[k + 1], F->v[0])));
+        double ln = norm(nrm);
+        if (ln <= 0.0) continue;
+        nrm = scl(nrm, 1.0 / ln);
+        double h = dot(sub(F->v[0], s), nrm);
+        for (int k = 1; k + 1 < F->nv; ++k)
+            K += h * tri_area_kernel(F->v[0], F->v[k], F->v[k + 1], s, m2, level);
+    }
+    return K;
+}
+
 /* ------------------------------------------------------------------------------------ */
 /* Geometry from the projection matrix                                                   */
 /* ------------------------------------------------------------------------------------ */
@@ -431,6 +471,24 @@ static void box_pixel_pair(const view_t *Vw, const double lo[3], const double hi
         }
     }
     out->Wrel = Wrel;
+}
+
+/* Truth of the area-averaged pixel value for one pair (Eq. integ with Eq. voxat): the area
+ * average over pixel (u, v) of the voxel's chord lengths. The detector-index area element
+ * per solid angle at a ray through x is |det M| (|x - s| / |w|)^3 with w = P2 . (x, 1), and
+ * dV = r^2 dr dOmega, so the average is |det M| int_cut |x - s| / |w|^3 dV; P2 . (x, 1) =
+ * M2 . (x - s) since M s + p4 = 0. */
+static double box_pixel_area_truth(const view_t *Vw, const double lo[3], const double hi[3], double u, double v) {
+    ptope_t P;
+    box_ptope(&P, lo, hi);
+    v3 n; double d;
+    pyramid_plane(Vw, 0, u - 0.5, +1.0, &n, &d); clip_ptope(&P, n, d);
+    pyramid_plane(Vw, 0, u + 0.5, -1.0, &n, &d); clip_ptope(&P, n, d);
+    pyramid_plane(Vw, 1, v - 0.5, +1.0, &n, &d); clip_ptope(&P, n, d);
+    pyramid_plane(Vw, 1, v + 0.5, -1.0, &n, &d); clip_ptope(&P, n, d);
+    if (!(ptope_volume(&P, NULL) > 0.0)) return 0.0;
+    v3 m2 = mk(Vw->P[2][0], Vw->P[2][1], Vw->P[2][2]);
+    return fabs(Vw->detM) * ptope_area_kernel(&P, Vw->s, m2, 0);
 }
 
 static void voxel_box(const grid_t *G, int i, int j, int k, double lo[3], double hi[3]) {
@@ -634,10 +692,11 @@ int or_backproject_voxels(int nx, int ny, int nz, double ax, double ay, double a
  * Candidate voxels: columns (i, j) whose base square is not entirely outside one of
  * the two column planes of the pixel, and for those the slices k that meet the z-range
  * of the row slab over the column's four vertical edges.
- * variant 0 / 1: the near-exact / relaxed pair weights W; variant 2: the truth integral
- * J = int_cut r^-2 dV of every pair (Eq. intcut) in place of W, so that with the exact
- * scaling the pixel value is the solid-angle average over the pixel of the line integrals
- * of the voxel volume (Eq. integub), with no sampling of rays. */
+ * variant 0 / 1: the near-exact / relaxed pair weights W. variant 2: the truth the scaled
+ * projection approximates, with no sampling of rays: for the exact scaling the solid-angle
+ * average over the pixel of the line integrals of the voxel volume (Eq. integub), the
+ * truth integral J = int_cut r^-2 dV of every pair (Eq. intcut) times 1 / abar; for the cos
+ * scaling their area average over the pixel (Eq. integ), box_pixel_area_truth per pair. */
 int or_project_pixels(int nx, int ny, int nz, double ax, double ay, double az, int nu, int nv,
                       const double *pmats, int nviews, int variant, int scaling,
                       const double *x, const int32_t *pix, int count, double *out) {
@@ -685,11 +744,15 @@ int or_project_pixels(int nx, int ny, int nz, double ax, double ay, double az, i
                     double lo[3], hi[3];
                     voxel_box(&G, i, j, k, lo, hi);
                     pair_t p;
+                    if (variant == 2 && scaling == 0) {
+                        acc += mu * box_pixel_area_truth(&V, lo, hi, pu, pv);
+                        continue;
+                    }
                     box_pixel_pair(&V, lo, hi, pu, pv, variant == 2 ? 1 : 0, &p);
                     acc += mu * (variant == 2 ? p.J : pair_weight(&p, variant));
                 }
             }
-        out[q] = acc * pixel_factor(&V, pu, pv, scaling);
+        out[q] = (variant == 2 && scaling == 0) ? acc : acc * pixel_factor(&V, pu, pv, scaling);
     }
     return err ? -1 : 0;
 }

@@ -19,7 +19,7 @@ _lock = threading.Lock()
 _lib = None
 
 EXACT, RELAXED = 0, 1
-TRUTH = 2          # project_pixels only: the truth integral J = int_cut r^-2 dV per pair
+TRUTH = 2          # project_pixels only: the exact pixel value the scaled projection approximates
 SCALE_COS, SCALE_EXACT = 0, 1
 
 
@@ -158,8 +158,10 @@ def backproject(geom, y, variant: int = EXACT, scaling: int = SCALE_COS) -> np.n
 
 def project_pixels(geom, x, pix, variant: int = EXACT, scaling: int = SCALE_COS) -> np.ndarray:
     """(A x) at selected pixels; pix int array [count, 3] of (view, v, u).
-    variant TRUTH replaces each pair weight by J = int_cut r^-2 dV: with the exact scaling
-    the value is then the solid-angle average of the line integrals over the pixel."""
+    variant TRUTH gives the value the projection approximates, with no ray sampling: for the
+    exact scaling the solid-angle average of the pixel's line integrals (pair weights
+    J = int_cut r^-2 dV), for the cos scaling their area average over the pixel (pair weights
+    |det M| int_cut |x - s| / |w|^3 dV, w the depth along the detector normal)."""
     x = _f64(x).reshape(geom.vol_shape)
     P = _f64(geom.pmats)
     pix = np.ascontiguousarray(pix, dtype=np.int32).reshape(-1, 3)
