@@ -1,10 +1,12 @@
 """Accuracy of the CUDA projector against the truth, at the benchmark workloads.
 
-With the exact scaling, the oracle's truth mode (pair weights J = int_cut r^-2 dV, Eq.
-intcut) gives the solid-angle average of the line integrals over each pixel (Eq. integub),
-the limit of ray integration. The CUDA kernels' error against it on sampled pixels of 8
-views is the variant's own approximation (Eq. vox with the cut's centre of mass for the
-near-exact weight, Eq. cutvolume for the relaxed one) plus float32 rounding. Printed with
+The oracle's truth mode gives the pixel value each scaling approximates, the limit of ray
+integration: the solid-angle average of the line integrals over the pixel for the exact
+scaling (Eq. integub, pair weights J = int_cut r^-2 dV of Eq. intcut), their area average for
+the cos scaling (Eq. integ). The CUDA kernels' error against it on sampled pixels of 8 views
+is the variant's own approximation (Eq. vox with the cut's centre of mass for the near-exact
+weight, Eq. cutvolume for the relaxed one; for the cos scaling also the pixel factor taken at
+the pixel centre) plus float32 rounding. Printed with
 `pytest -s`; asserted: the near-exact kernel stays within float32 rounding of the truth and
 the relaxed kernel is measurably further off (measured on a B300: 12x at the 20 degree cone,
 24-33x at the other two workloads).
@@ -16,35 +18,36 @@ import torch
 import oracle
 from paper_2110_09841_b300 import inputs
 from paper_2110_09841_b300.kct import Projector
-from test_oracle_accuracy import ACCURACY_WORKLOADS, rel_l2, signal_pixels
+from test_oracle_accuracy import ACCURACY_WORKLOADS, rel_l2, signal_pixels, workload_phantom64
 
 pytestmark = pytest.mark.gpu
 
 
+@pytest.mark.parametrize("sname,scaling", [("exact", oracle.SCALE_EXACT), ("cos", oracle.SCALE_COS)])
 @pytest.mark.parametrize("name", ACCURACY_WORKLOADS)
-def test_kernels_against_the_truth(name):
+def test_kernels_against_the_truth(name, sname, scaling):
     g = inputs.workload_geometry(name)
     views = list(range(0, g.nviews, g.nviews // 8))[:8]
     g8 = g.subset_views(views)
-    x = inputs.workload_phantom(name, device="cuda")
-    x64 = x.cpu().double().numpy()
+    x64 = workload_phantom64(name)
+    x = torch.as_tensor(x64, dtype=torch.float32).cuda()
     pix = signal_pixels(g, views, 25, 31)
-    truth = oracle.project_pixels(g, x64, pix, oracle.TRUTH, oracle.SCALE_EXACT)
+    truth = oracle.project_pixels(g, x64, pix, oracle.TRUTH, scaling)
     keep = truth > 0.05 * truth.max()
     assert keep.sum() > 150
     local = pix.copy()
     local[:, 0] = [views.index(v) for v in pix[:, 0]]
     err = {}
     for vname, variant in (("exact", oracle.EXACT), ("relaxed", oracle.RELAXED)):
-        A = Projector(g8, vname, "exact")
+        A = Projector(g8, vname, sname)
         b = A.project(x)
         torch.cuda.synchronize()
         assert A.device_error() == 0
         got = b[local[:, 0], local[:, 1], local[:, 2]].cpu().double().numpy()
-        ref = oracle.project_pixels(g, x64, pix, variant, oracle.SCALE_EXACT)
+        ref = oracle.project_pixels(g, x64, pix, variant, scaling)
         err[vname] = rel_l2(got[keep], truth[keep])
         d = np.abs(got[keep] - truth[keep]) / truth[keep]
-        print(f"{name} {vname}: kernel vs truth rel L2 {err[vname]:.2e} (max {d.max():.2e}); "
+        print(f"{name} {vname}/{sname}: kernel vs truth rel L2 {err[vname]:.2e} (max {d.max():.2e}); "
               f"oracle variant vs truth {rel_l2(ref[keep], truth[keep]):.2e}; "
               f"kernel vs oracle variant {rel_l2(got[keep], ref[keep]):.2e}")
     assert err["exact"] <= 5e-6, err
