@@ -385,10 +385,6 @@ kct_status kct_plan_create(kct_plan** out, const kct_volume_desc* vol, const kct
     p->d_err = nullptr;
     p->d_count = nullptr;
     p->fwd_chunk = kct::VIEW_CHUNK;
-    // relaxed adjoint: two runs per brick where (almost) every brick's footprint fits the tile
-    p->bwd_runs = (variant == KCT_CVP_RELAXED &&
-                   brick_overflow(pmats, nviews, *vol, *det, kct::Brick<1, false, 2>::Z, kct::Brick<1, false, 2>::TILE) <= 0.02)
-                      ? 2 : 1;
     p->h_views.resize(nviews);
     for (int q = 0; q < nviews; ++q) {
         std::string why = setup_view(pmats + 12 * q, *vol, p->h_views[q]);
@@ -400,6 +396,11 @@ kct_status kct_plan_create(kct_plan** out, const kct_volume_desc* vol, const kct
             return fail(unsup ? KCT_ERR_UNSUPPORTED : KCT_ERR_GEOMETRY, buf + why);
         }
     }
+    // relaxed adjoint: two runs per brick where (almost) every brick's footprint fits the tile
+    // (after the views are validated: the whole volume is then in front of the source)
+    p->bwd_runs = (variant == KCT_CVP_RELAXED &&
+                   brick_overflow(pmats, nviews, *vol, *det, kct::Brick<1, false, 2>::Z, kct::Brick<1, false, 2>::TILE) <= 0.02)
+                      ? 2 : 1;
     Grid& G = p->grid;
     G.nx = vol->nx; G.ny = vol->ny; G.nz = vol->nz;
     G.nu = det->nu; G.nv = det->nv; G.nviews = nviews;
