@@ -171,6 +171,28 @@ def test_elevated_source_thin_slivers(vname, variant):
     assert A.device_error() == 0
 
 
+@pytest.mark.parametrize("vname,variant", VARIANTS)
+def test_largest_footprints(vname, variant):
+    """Voxels near the largest footprint the kernels take: 1 mm voxels at magnification 1.5
+    on 0.15 x 0.065 mm pixels span 24-28 detector rows (the per-voxel bound is 31) and 12-16
+    columns (two or three column-cut passes); a lane walks that many rows per column cut, the
+    faces of a 64-voxel run are crossed by 150-210 row planes (several evaluation rounds of a
+    warp), 66 voxels along x_3 fill both runs of a brick, and every brick overflows the shared
+    tile. Forward, adjoint and the adjoint identity against the oracle, element by element."""
+    g = inputs.make_geometry((3, 3, 66), (1.0, 1.0, 1.0), (64, 1600), (0.15, 0.065), 2, 300.0, 450.0, 75.0)
+    x = np.random.default_rng(41).random(g.vol_shape)
+    y = np.random.default_rng(42).random(g.proj_shape)
+    A = Projector(g, vname, "cos")
+    b = A.project(dev(x)).cpu().numpy()
+    assert_close_per_view(b, oracle.project(g, x, variant, 0))
+    xb = A.backproject(dev(y)).cpu().numpy()
+    assert_close_volume(xb, oracle.backproject(g, y, variant, 0))
+    assert A.device_error() == 0
+    lhs = float((b.astype(np.float64) * y).sum())
+    rhs = float((x * xb.astype(np.float64)).sum())
+    assert abs(lhs - rhs) / max(abs(lhs), abs(rhs)) <= 1e-5
+
+
 def test_volume_off_detector_gives_zeros():
     # a detector far off to the side: no voxel projects onto it
     P = inputs.circular_pmats(2, 300.0, 500.0, 16, 16, 0.5, 0.5, cu=-400.0)
