@@ -96,8 +96,10 @@ _PHANTOMS = {}
 
 
 def workload_phantom64(name):
-    """The workload's seeded phantom in float64 (cached: the two 512^3 workloads share it)."""
+    """The workload's seeded phantom in float64; the last one is kept (the tests of one
+    workload follow each other, and a 512^3 phantom holds 1 GB)."""
     if name not in _PHANTOMS:
+        _PHANTOMS.clear()
         _PHANTOMS[name] = inputs.workload_phantom(name).numpy().astype(np.float64)
     return _PHANTOMS[name]
 
